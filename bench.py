@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark: device-timed GFLOP/s (Eq. 1, 2*M*N*K/t) of one grouped launch
+over the uneven batch -- 200,000 FP32 instances with M, N, K log-uniform on
+[1, 80], all four cases, ld = rows + U{0..7} -- with its roofline fraction,
+the end-to-end rate through the C ABI from pinned host memory, and the FP64
+CPU oracle as the reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision ffma]
+    python bench.py --impl reference ...   # the CPU oracle arm
+
+One step = one execution of the whole plan (one persistent kernel launch,
+replayed from a CUDA graph).  The pools (about 1.3 GB) are larger than the
+129 MB L2, so no flush is needed between steps.  Under torchrun each rank runs
+its own copy of the batch (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "small-GEMM GFLOP/s & roofline % (uneven batch), TC split vs plain FP32 @1e-5"
+WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT/TN/TT uniform "
+            "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
+NOMINAL_HBM_GBS = 8000.0
+PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_09822_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"grouped_{precision}_uneven200k.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    kv = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": float(max(maxes)),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def cpu_baseline_leg(batch, gpu_result, min_seconds):
+    """The CPU-baseline leg: time the FP64 oracle over the whole batch
+    (repeated until min_seconds), and use its result to measure the error of
+    the GPU's first launch."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_util import errors
+    flops = batch.flops()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        ref, _ = oracle.gemm_batch(batch)
+        reps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    cpu = {"value": flops * reps / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"the whole batch, {reps} pass(es) in {dt:.1f} s, FP64 triple loop"}
+    err = errors(batch, gpu_result, ref)
+    err["against"] = "FP64 oracle, all instances of the first launch"
+    return cpu, err
+
+
+def run_reference(args):
+    """CPU oracle arm: FP64 triple loop over the same batch on the host cores."""
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2208_09822_gb300 import workloads as W
+    batch = W.uneven()
+    # one step = the oracle over a bounded sample of the batch (every 8th instance)
+    sample = batch.select(np.arange(0, batch.count, 8))
+    flops = sample.flops()
+    for _ in range(args.warmup):
+        oracle.gemm_batch(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gemm_batch(sample)
+    dt = time.perf_counter() - t0
+    value = flops * args.steps / dt / 1e9
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.format(n=batch.count), "sample": f"every 8th instance ({sample.count} instances, "
+                                                   f"{flops / 1e9:.3f} GFLOP) per step"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"every 8th instance of the batch ({sample.count}), FP64 triple loop"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
+    ap.add_argument("--precision", default="ffma", choices=sorted(PRECISIONS))
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=200_000,
+                    help="instances of the uneven batch (smaller only for profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_2208_09822_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2208_09822_gb300 import iaat
+    from paper_2208_09822_gb300 import workloads as W
+
+    batch = W.uneven(count=args.instances)
+    prec = PRECISIONS[args.precision]
+    tA = torch.from_numpy(batch.A).to(dev)
+    tB = torch.from_numpy(batch.B).to(dev)
+    tC = torch.from_numpy(batch.C).to(dev)
+    C0 = tC.clone()
+    descs = iaat.descs_for_pools(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+    plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, prec)
+    info = iaat.iaat_plan_info(plan)
+    stream = torch.cuda.Stream(device=dev)
+
+    # first launch; its result is checked against the oracle in the CPU leg
+    with torch.cuda.stream(stream):
+        iaat.iaat_gemm_grouped(plan, stream)
+    iaat.iaat_plan_check(plan, stream)
+    first_result = tC.cpu().numpy() if rank == 0 else None
+
+    # graph of one launch, replayed
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        iaat.iaat_gemm_grouped(plan, stream)
+    tC.copy_(C0)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.25)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):   # replay() launches on the current stream
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    iaat.iaat_plan_check(plan, stream)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    flops = info["flops"]
+    value = flops * world / (ms * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    abytes = info["algorithmic_bytes"]
+    achieved = abytes / (ms * 1e-3) / 1e9
+    roof_gflops = abytes and flops / abytes * NOMINAL_HBM_GBS
+
+    # end to end through the C ABI: pinned host -> device, launch, C -> host
+    hA = torch.from_numpy(batch.A).pin_memory()
+    hB = torch.from_numpy(batch.B).pin_memory()
+    hC = torch.from_numpy(batch.C).pin_memory()
+    hOut = torch.empty_like(hC).pin_memory()
+    h2d = hA.numel() * hA.element_size() + hB.numel() * hB.element_size() + hC.numel() * hC.element_size()
+    d2h = hOut.numel() * hOut.element_size()
+    with torch.cuda.stream(stream):
+        tA.copy_(hA, non_blocking=True); tB.copy_(hB, non_blocking=True); tC.copy_(hC, non_blocking=True)
+        iaat.iaat_gemm_grouped(plan, stream)
+        hOut.copy_(tC, non_blocking=True)
+    torch.cuda.synchronize()
+    args.e2e_steps = max(1, args.e2e_steps)
+    if world > 1:
+        dist.barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.e2e_steps):
+            tA.copy_(hA, non_blocking=True)
+            tB.copy_(hB, non_blocking=True)
+            tC.copy_(hC, non_blocking=True)
+            iaat.iaat_gemm_grouped(plan, stream)
+            hOut.copy_(tC, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
+    iaat.iaat_plan_check(plan, stream)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = flops * world / (e2e_ms * 1e-3) / 1e9
+
+    if rank == 0:
+        cpu, err = None, None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu, err = cpu_baseline_leg(batch, first_result, 10.0)
+        traffic = profile_traffic(args.precision)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(n=batch.count), "instances": batch.count, "precision": args.precision,
+                       "parallelism": f"instances x{world} (one batch per GPU)",
+                       "l2": "inputs larger than L2 (pools %.2f GB > 129 MB); no flush" %
+                             ((batch.A.nbytes + batch.B.nbytes + batch.C.nbytes) / 1e9),
+                       "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
+                       "grid": info["grid"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "algorithmic_bytes_per_launch": abytes,
+                         "roofline_gflops_at_8TBs": roof_gflops,
+                         "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": args.steps * info["kernels"],
+            "clocks": clocks,
+            "error": err,
+        }
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

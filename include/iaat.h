@@ -1,0 +1,193 @@
+/*
+ * iaat.h -- C ABI of the GB300 small-GEMM library (after IAAT, arXiv
+ * 2208.09822).
+ *
+ * Operation (Sec. I of the paper):  C = alpha * op(A) * op(B) + beta * C
+ *   C is M x N, op(A) is M x K, op(B) is K x N.
+ *   op(X) = X (IAAT_OP_N) or X^T (IAAT_OP_T).  The case names NN/NT/TN/TT give
+ *   A's op first, B's second (note under Table I).
+ *   Storage is column-major (note under Table I): element (i, j) of a stored
+ *   matrix X with leading dimension ldx is X[i + j * ldx].  The stored A is
+ *   M x K (op N) or K x M (op T); the stored B is K x N (op N) or N x K (op T).
+ *
+ * Domain (Sec. I and Sec. VI): cbrt(M*N*K) <= 80, or <= 32 for the TN case.
+ *   It is checked in integer form, M*N*K <= 512000 (TN: <= 32768); larger
+ *   problems are refused with IAAT_ERR_NOT_SMALL and never computed.
+ *
+ * Argument rules (reference-BLAS xGEMM conventions; the paper is silent):
+ *   M, N, K >= 0;  lda >= max(1, transA ? K : M);  ldb >= max(1, transB ? N : K);
+ *   ldc >= max(1, M).  M == 0 or N == 0: nothing is done.  alpha == 0 or
+ *   K == 0: C = beta * C and A, B are not read.  beta == 0: C is not read, so
+ *   NaN or Inf already in C does not reach the result.  Elements of C outside
+ *   its M x N part (the ld padding) are never written.  FP32 pointers must be
+ *   4-byte aligned and FP64 pointers 8-byte aligned (IAAT_ERR_MISALIGNED).
+ *   A, B and C of one call or one plan must not overlap in written memory.
+ *
+ * Memory and execution:
+ *   Every A, B, C pointer is a DEVICE pointer owned by the caller.  All work
+ *   is enqueued on the caller's stream (a cudaStream_t passed as void*, NULL
+ *   for the legacy default stream) and returns without waiting for the GPU.
+ *   No exception crosses this ABI; every entry point returns a status, and
+ *   iaat_last_error() gives a message for the calling thread's last failure.
+ *   On any error status nothing has been enqueued.
+ *
+ * The library reads, as 16-byte-aligned blocks, the aligned 16-byte granules
+ * that contain the elements of A, B and C it needs; bytes of those granules
+ * outside the matrices are read but never used or written (a granule never
+ * crosses a page, so this cannot fault).
+ */
+#ifndef IAAT_H
+#define IAAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { IAAT_OP_N = 0, IAAT_OP_T = 1 } iaat_op_t;
+
+typedef enum { IAAT_F32 = 0, IAAT_F64 = 1 } iaat_dtype_t;
+
+/* Arithmetic used for an FP32 plan (FP64 plans accept only the default).
+ * DEFAULT: FP32 FFMA on the CUDA cores (FP64: DFMA).
+ * 3XBF16:  tcgen05 tensor cores, X = Xh + Xl with Xh = bf16(X), Xl =
+ *          bf16(X - Xh); Ah*Bh + Ah*Bl + Al*Bh accumulated in FP32.
+ * TF32:    tcgen05 kind::tf32 on round-to-nearest TF32 inputs, FP32 accumulate.
+ * FP16:    tcgen05 kind::f16 on FP16-rounded inputs, FP32 accumulate. */
+typedef enum {
+    IAAT_PREC_DEFAULT = 0,
+    IAAT_PREC_3XBF16 = 1,
+    IAAT_PREC_TF32 = 2,
+    IAAT_PREC_FP16 = 3
+} iaat_precision_t;
+
+typedef enum {
+    IAAT_OK = 0,
+    IAAT_ERR_INVALID_VALUE = 1,   /* bad size, leading dimension, pointer or enum */
+    IAAT_ERR_NOT_SMALL = 2,       /* outside the small-GEMM domain */
+    IAAT_ERR_MISALIGNED = 3,      /* pointer not aligned to its element size */
+    IAAT_ERR_UNSUPPORTED = 4,     /* combination not built (e.g. FP64 + 3XBF16) */
+    IAAT_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    IAAT_ERR_DEVICE_TIMEOUT = 6,  /* a kernel gave up waiting and stopped early */
+    IAAT_ERR_OOM = 7              /* device or host allocation failed */
+} iaat_status_t;
+
+/* One GEMM instance of a grouped call.  alpha and beta are rounded to the
+ * plan's type.  transA / transB take iaat_op_t values. */
+typedef struct {
+    int32_t M, N, K;
+    int32_t lda, ldb, ldc;
+    int32_t transA, transB;
+    double alpha, beta;
+    const void *A;
+    const void *B;
+    void *C;
+} iaat_gemm_desc_t;
+
+typedef struct iaat_plan_s *iaat_plan_t;
+
+/* Optional knobs of iaat_plan_create (pass NULL for the tuned defaults).
+ * Zero in any field means "use the tuned default". */
+typedef struct {
+    int32_t ctas_per_sm;       /* persistent CTAs per SM (the kernel uses 1) */
+    int32_t max_group_tasks;   /* tasks in one pipeline stage (<= 32) */
+    int32_t force_variant;     /* 0: tiler's choice; k > 0: register-tile variant k-1 */
+    int32_t inject_fault;      /* testing only: 1 = corrupt the first stage's task
+                                  count so the kernel must detect it, give up and
+                                  report IAAT_ERR_DEVICE_TIMEOUT via iaat_plan_check */
+    int32_t reserved[4];
+} iaat_plan_options_t;
+
+/* Statistics of a plan (iaat_plan_info). */
+typedef struct {
+    int64_t instances;         /* descriptors passed in */
+    int64_t active;            /* instances that need work */
+    int64_t tasks;             /* work pieces after splitting */
+    int64_t groups;            /* pipeline stages */
+    int64_t blocks;            /* warp blocks over all tasks */
+    int64_t flops;             /* sum of 2*M*N*K over active instances (Eq. 1) */
+    int64_t algorithmic_bytes; /* A, B, C written, C read when beta != 0 */
+    int64_t plan_bytes;        /* device bytes the plan holds (descriptors) */
+    int32_t grid;              /* CTAs of each launch */
+    int32_t kernels;           /* kernels one iaat_gemm_grouped launches */
+    int32_t dtype, precision;
+} iaat_plan_info_t;
+
+/* Single small GEMM, FP32 / FP64 (BLAS sgemm/dgemm argument order, Sec. I).
+ * Device pointers; asynchronous on `stream`.  The instance's tasks travel in
+ * the kernel's parameter block, so the call allocates nothing; a device-side
+ * time-out is reported by iaat_plan_check(NULL, stream).  For the paper's
+ * "same size repeatedly" use (Sec. VII), a plan (iaat_plan_create) keeps the
+ * tiling and descriptors on the device and replays them. */
+iaat_status_t iaat_sgemm(int transA, int transB, int M, int N, int K,
+                         float alpha, const float *A, int lda,
+                         const float *B, int ldb, float beta, float *C,
+                         int ldc, void *stream);
+iaat_status_t iaat_dgemm(int transA, int transB, int M, int N, int K,
+                         double alpha, const double *A, int lda,
+                         const double *B, int ldb, double beta, double *C,
+                         int ldc, void *stream);
+
+/* Build a plan for `count` instances (host array `descs`, device pointers
+ * inside): validates every instance (the first failure's index is in
+ * iaat_last_error), tiles each one into warp blocks (run-time stage,
+ * Sec. V-A), groups the pieces into pipeline stages, orders them for the
+ * persistent schedule and copies the descriptors to the device (synchronous;
+ * uses the current CUDA device).  The plan keeps the pointers: re-plan when
+ * they change.  `opts` may be NULL. */
+iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t count,
+                               iaat_dtype_t dtype, iaat_precision_t precision,
+                               const iaat_plan_options_t *opts,
+                               iaat_plan_t *out);
+
+/* Enqueue one execution of the plan (the kernel executing plan, Sec. V-B) on
+ * `stream`: one persistent kernel launch, no host synchronisation and no
+ * allocation, so it can be captured in a CUDA graph. */
+iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream);
+
+/* Synchronise `stream`, then report (and clear) a device-side error of the
+ * plan's kernels: IAAT_ERR_DEVICE_TIMEOUT if a bounded wait gave up. */
+iaat_status_t iaat_plan_check(iaat_plan_t plan, void *stream);
+
+iaat_status_t iaat_plan_info(iaat_plan_t plan, iaat_plan_info_t *info);
+
+/* Free the plan's device memory (synchronises the device first). */
+iaat_status_t iaat_plan_destroy(iaat_plan_t plan);
+
+/* Time the register-tile variants on the current GPU for (dtype, precision)
+ * and write the per-shape-class winners as JSON to `cache_path` (NULL: the
+ * path in IAAT_TUNE_CACHE, else no file).  Later plans read the cache named
+ * by IAAT_TUNE_CACHE.  Synchronous; allocates its own test matrices. */
+iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t precision,
+                            const char *cache_path);
+
+/* Host-only view of the run-time tiler (no GPU needed).  Tiles one M x N
+ * (x K) instance of the given type and case with the library's register-tile
+ * variants and writes up to `cap` blocks as (row0, col0, rows, cols)
+ * quadruples to `blocks`.  Returns the number of blocks (may exceed `cap`),
+ * or -1 on bad arguments. */
+int64_t iaat_tile(iaat_dtype_t dtype, int transA, int transB, int M, int N,
+                  int K, int32_t *blocks, int64_t cap);
+
+/* Host-only exact-cover tiler under the paper's memops objective (Sec. V-A,
+ * "Minimal Memops"): tile an M x N C into row strips whose heights are the
+ * `nheights` entries of `heights`, each strip cut into blocks of widths
+ * 1..max_width[h] of that height, minimising sum(m_i + n_i).  Writes up to
+ * `cap` quadruples to `blocks`; returns the block count, or -1 when no exact
+ * cover exists or the arguments are bad.  `*sum_out` receives sum(m_i+n_i). */
+int64_t iaat_tile_exact(int M, int N, const int32_t *heights,
+                        const int32_t *max_width, int nheights,
+                        int32_t *blocks, int64_t cap, int64_t *sum_out);
+
+/* Version string of this build. */
+const char *iaat_version(void);
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *iaat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IAAT_H */

@@ -1,0 +1,234 @@
+// Definitions shared by the host planner and the device kernels.
+//
+// Work model (the GPU form of the paper's two stages):
+//  * install time (Sec. IV): a fixed family of warp-level register-tile
+//    kernels, one per (MR x NR register tile, LM x LN lane grid), compiled
+//    ahead of time for sm_103a -- the "kernel array" of Table I;
+//  * run time (Sec. V): the host tiler splits each instance's C into warp
+//    blocks of one variant (the input-aware choice), the planner packs the
+//    pieces into pipeline stages, and one persistent kernel executes the
+//    whole plan (the "kernel executing plan", Sec. V-B).
+#pragma once
+#include <cstdint>
+#include <cstddef>
+
+#if defined(__CUDACC__)
+#define IAAT_HD __host__ __device__ __forceinline__
+#define IAAT_CE __host__ __device__ constexpr
+#else
+#define IAAT_HD inline
+#define IAAT_CE constexpr
+#endif
+
+namespace iaat {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxDim = 80;          // cbrt(MNK) <= 80 bounds every size used here
+constexpr int kMaxGroupTasks = 32;   // tasks per pipeline stage (one per producer lane)
+constexpr int kNumSlots = 8;         // pipeline stages in flight per CTA
+constexpr int kConsumerWarps = 8;    // compute warps per CTA
+constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+
+// One piece of work: a whole instance, or a column range of it.  Pointers
+// address element (0,0) of the piece's stored A, B, C.  64 bytes.
+struct alignas(16) TaskDesc {
+    const char *A;
+    const char *B;
+    char *C;
+    int32_t lda, ldb, ldc;
+    int16_t M, N, K;      // C rows, C columns of this piece; K = 0: no product
+    uint8_t ta, tb;
+    uint8_t variant;      // register-tile variant of every block of the piece
+    uint8_t flags;        // bit 0: beta != 0 (C is read)
+    uint8_t nbm, nbn;     // warp blocks along M and along N
+    double alpha, beta;
+};
+static_assert(sizeof(TaskDesc) == 64, "TaskDesc layout");
+constexpr uint8_t kFlagReadC = 1;
+
+// What the consumer warps see of a task once its operands sit in shared
+// memory: element (i, j) of the stored X is at byte off + j*cs + i*esz.
+struct alignas(16) TaskRec {
+    char *C;
+    int32_t ldc;
+    int32_t offA, offB, offC;
+    int32_t csA, csB, csC;
+    int16_t M, N, K;
+    uint8_t ta, tb, variant, flags, nbm, nbn;
+    double alpha, beta;
+};
+static_assert(sizeof(TaskRec) == 64, "TaskRec layout");
+
+struct alignas(16) SlotHeader {
+    int32_t ntasks;
+    int32_t nblocks;
+    int32_t pad[2];
+    int32_t prefix[kMaxGroupTasks];  // inclusive prefix of blocks per task
+};
+constexpr int kSlotBytes = sizeof(SlotHeader) + kMaxGroupTasks * sizeof(TaskRec);
+
+// ----------------------------------------------- raw staging of a matrix
+// A stored sub-matrix (h rows, w columns, leading dimension ld elements)
+// starting at address p is copied into shared memory as whole aligned
+// 16-byte granules: either as one span from the granule of its first element
+// to the granule of its last (span mode), or column by column (column mode,
+// when the ld padding would make the span much larger than the data).  In
+// both modes element (i, j) lands at  base + (p & 15) + j*cs + i*esz,  so
+// global and shared addresses agree modulo 16 and every copy is a legal
+// 16-byte-aligned bulk copy.
+struct Stage {
+    uint32_t bytes;      // shared bytes reserved (multiple of 16)
+    uint32_t cs;         // column stride in shared memory (bytes)
+    uint32_t copies;     // bulk copies issued
+    uint32_t tx;         // bytes the copies deliver
+    uint8_t span;        // 1: one span copy
+};
+
+IAAT_HD uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~(uint64_t)15); }
+
+IAAT_HD Stage plan_stage(uint64_t p, int h, int w, int ld, int esz)
+{
+    Stage s{0, 0, 0, 0, 1};
+    if (h <= 0 || w <= 0)
+        return s;
+    uint64_t beg = p & ~(uint64_t)15;
+    uint64_t last = p + ((uint64_t)(w - 1) * (uint64_t)ld + (uint64_t)h) * (uint64_t)esz;
+    uint32_t span = (uint32_t)(((last + 15) & ~(uint64_t)15) - beg);
+    uint32_t ldb = (uint32_t)ld * (uint32_t)esz;
+    uint32_t cs = round16((uint64_t)h * esz + 32) + (ldb & 15u);
+    uint32_t head = (uint32_t)(p & 15);
+    uint32_t colbytes = round16((uint64_t)head + (uint64_t)(w - 1) * cs + (uint64_t)h * esz);
+    if (w == 1 || (uint64_t)span <= (uint64_t)colbytes + (colbytes >> 3) + 256) {
+        s.bytes = span; s.cs = ldb; s.copies = 1; s.tx = span; s.span = 1;
+    } else {
+        s.bytes = colbytes; s.cs = cs; s.copies = (uint32_t)w; s.span = 0;
+        // each column delivers the granules covering its own elements
+        uint32_t tx = 0;
+        for (int j = 0; j < w; ++j) {
+            uint64_t c0 = p + (uint64_t)j * ldb;
+            uint64_t c1 = c0 + (uint64_t)h * esz;
+            tx += (uint32_t)(((c1 + 15) & ~(uint64_t)15) - (c0 & ~(uint64_t)15));
+        }
+        s.tx = tx;
+    }
+    return s;
+}
+
+// Stored shapes of a task's operands.
+IAAT_HD void stored_dims(const TaskDesc &t, int &ha, int &wa, int &hb, int &wb)
+{
+    ha = t.ta ? t.K : t.M; wa = t.ta ? t.M : t.K;
+    hb = t.tb ? t.N : t.K; wb = t.tb ? t.K : t.N;
+}
+
+struct TaskStages {
+    Stage a, b, c;
+    IAAT_HD uint32_t total() const { return a.bytes + b.bytes + c.bytes; }
+};
+
+IAAT_HD TaskStages plan_task(const TaskDesc &t, int esz)
+{
+    TaskStages s;
+    int ha, wa, hb, wb;
+    stored_dims(t, ha, wa, hb, wb);
+    bool prod = t.K > 0;
+    s.a = plan_stage((uint64_t)(uintptr_t)t.A, prod ? ha : 0, prod ? wa : 0, t.lda, esz);
+    s.b = plan_stage((uint64_t)(uintptr_t)t.B, prod ? hb : 0, prod ? wb : 0, t.ldb, esz);
+    bool readc = (t.flags & kFlagReadC) != 0;
+    s.c = plan_stage((uint64_t)(uintptr_t)t.C, readc ? t.M : 0, readc ? t.N : 0, t.ldc, esz);
+    return s;
+}
+
+// ------------------------------------------- register-tile kernel family
+// Variant v: every lane holds an MR x NR tile of C; the 32 lanes form an
+// LM x LN grid, so one warp block covers (LM*MR) x (LN*NR) of C.  This is the
+// GPU counterpart of Table I's m_c x n_c kernels: each is fully unrolled for
+// its tile, and the tiler picks one per instance.
+struct Variant {
+    int8_t mr, nr, lm, ln;
+};
+
+// FP32 family.
+constexpr int kNumVariantsF32 = 12;
+constexpr Variant kVariantsF32[kNumVariantsF32] = {
+    {4, 8, 8, 4},   // 0: 32 x 32
+    {4, 4, 8, 4},   // 1: 32 x 16
+    {4, 4, 4, 8},   // 2: 16 x 32
+    {2, 4, 8, 4},   // 3: 16 x 16
+    {2, 2, 8, 4},   // 4: 16 x 8
+    {2, 2, 4, 8},   // 5: 8 x 16
+    {1, 2, 8, 4},   // 6: 8 x 8
+    {1, 1, 8, 4},   // 7: 8 x 4
+    {1, 1, 4, 8},   // 8: 4 x 8
+    {1, 1, 32, 1},  // 9: 32 x 1
+    {1, 1, 1, 32},  // 10: 1 x 32
+    {8, 8, 4, 8},   // 11: 32 x 64
+};
+
+// FP64 family (DFMA; each accumulator takes two registers).
+constexpr int kNumVariantsF64 = 10;
+constexpr Variant kVariantsF64[kNumVariantsF64] = {
+    {4, 8, 8, 4},   // 0: 32 x 32
+    {4, 4, 8, 4},   // 1: 32 x 16
+    {4, 4, 4, 8},   // 2: 16 x 32
+    {2, 4, 8, 4},   // 3: 16 x 16
+    {2, 2, 8, 4},   // 4: 16 x 8
+    {2, 2, 4, 8},   // 5: 8 x 16
+    {1, 1, 8, 4},   // 6: 8 x 4
+    {1, 1, 4, 8},   // 7: 4 x 8
+    {1, 1, 32, 1},  // 8: 32 x 1
+    {1, 1, 1, 32},  // 9: 1 x 32
+};
+
+// K is consumed in chunks of kKC (FP32) / kKC64 (FP64) staged per warp.
+constexpr int kKC = 16;
+constexpr int kKC64 = 8;
+constexpr int kMaxBM = 32, kMaxBN = 64;  // largest warp block over both families
+
+// Per-warp canonical operand buffers: As[KC][BM], Bs[KC][BN].
+template <int ESZ> struct Traits;
+template <> struct Traits<4> {
+    static constexpr int KC = kKC;
+    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 4;   // 6 KB
+};
+template <> struct Traits<8> {
+    static constexpr int KC = kKC64;
+    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 8;   // 6 KB
+};
+
+// Shared-memory map of the persistent kernel (byte offsets).
+constexpr int kSmemBarriers = 0;                          // full[], empty[]
+constexpr int kSmemSlots = 256;
+constexpr int kSmemCanon = kSmemSlots + kNumSlots * kSlotBytes;
+template <int ESZ> IAAT_CE int smem_ring_offset()
+{
+    return ((kSmemCanon + kConsumerWarps * Traits<ESZ>::kCanonBytes) + 127) & ~127;
+}
+constexpr int kSmemTotal = 227 * 1024;
+template <int ESZ> IAAT_CE int ring_bytes() { return (kSmemTotal - smem_ring_offset<ESZ>()) & ~127; }
+// A stage may take at most half the ring, so two always fit.
+template <int ESZ> IAAT_CE int max_group_bytes() { return ring_bytes<ESZ>() / 2; }
+
+// Kernel parameters.
+struct Params {
+    const TaskDesc *tasks;
+    const int32_t *gbeg;      // group g = tasks [gbeg[g], gbeg[g+1])
+    int32_t ngroups;
+    int32_t pad;
+    int32_t *err;             // device error word (0 = fine)
+};
+
+// Kernel parameters: either plan arrays in global memory, or (single call)
+// up to kInline tasks carried inline in the parameter block.
+constexpr int kInline = 8;
+struct KParams {
+    Params p;
+    TaskDesc inline_tasks[kInline];
+    int32_t inline_gbeg[kInline + 1];
+};
+
+constexpr int32_t kErrTimeoutFull = 1;
+constexpr int32_t kErrTimeoutEmpty = 2;
+constexpr int32_t kErrBadGroup = 4;
+
+}  // namespace iaat

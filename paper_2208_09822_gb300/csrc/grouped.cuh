@@ -1,0 +1,480 @@
+// Persistent grouped small-GEMM kernel on the CUDA cores (FP32 FFMA, FP64
+// DFMA): the "kernel executing plan" of Sec. V-B run by one launch.
+//
+// Each CTA walks its share of the plan's stages (groups of <= 32 tasks):
+//  * the producer warp (one lane per task) sizes each task's A, B, C, claims
+//    a contiguous piece of the shared-memory ring, publishes the task records
+//    and issues 1-D bulk copies that complete on the stage's mbarrier;
+//  * the consumer warps take the stage's warp blocks round-robin.  A block is
+//    computed K-chunk by K-chunk: the warp re-packs op(A) rows and op(B)
+//    columns of the chunk into its own canonical buffers (zero-padded, so the
+//    inner loop has no bounds checks -- the paper's "no boundary processing"),
+//    then every lane runs its MR x NR register tile as rank-1 updates
+//    (Algorithm 1's k-loop), and finally writes alpha*acc + beta*C0.
+// Every wait is bounded; on time-out the kernel records an error code in
+// *err and stops instead of hanging.
+#pragma once
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace iaat {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ int sched_group(int i, int cta, int ncta)
+{
+    // snake order over cost-sorted groups: balances like LPT without atomics
+    return i * ncta + ((i & 1) ? (ncta - 1 - cta) : cta);
+}
+
+__device__ __forceinline__ void set_error(int32_t *err, int32_t code)
+{
+    if (err)
+        atomicOr(err, code);
+}
+
+struct SmemMap {
+    char *base;
+    uint32_t sbase;
+    __device__ uint32_t full(int s) const { return sbase + kSmemBarriers + 8 * s; }
+    __device__ uint32_t empty(int s) const { return sbase + kSmemBarriers + 64 + 8 * s; }
+    __device__ uint32_t *range_beg() const { return reinterpret_cast<uint32_t *>(base + 128); }
+    __device__ uint32_t *range_end() const { return reinterpret_cast<uint32_t *>(base + 160); }
+    __device__ SlotHeader *header(int s) const
+    {
+        return reinterpret_cast<SlotHeader *>(base + kSmemSlots + s * kSlotBytes);
+    }
+    __device__ TaskRec *recs(int s) const
+    {
+        return reinterpret_cast<TaskRec *>(base + kSmemSlots + s * kSlotBytes + sizeof(SlotHeader));
+    }
+};
+
+__device__ __forceinline__ void issue_stage(const Stage &st, const char *p, int h, int w, int ld, int esz,
+                                            uint32_t dst, uint32_t bar)
+{
+    if (st.bytes == 0)
+        return;
+    uint64_t pa = reinterpret_cast<uint64_t>(p);
+    if (st.span) {
+        bulk_g2s(dst, reinterpret_cast<const void *>(pa & ~15ull), st.bytes, bar);
+        return;
+    }
+    uint32_t head = (uint32_t)(pa & 15);
+    uint64_t ldb = (uint64_t)ld * esz;
+    for (int j = 0; j < w; ++j) {
+        uint64_t c0 = pa + (uint64_t)j * ldb;
+        uint64_t g0 = c0 & ~15ull;
+        uint64_t g1 = (c0 + (uint64_t)h * esz + 15) & ~15ull;
+        uint32_t d = dst + ((head + (uint32_t)j * st.cs) & ~15u);
+        bulk_g2s(d, reinterpret_cast<const void *>(g0), (uint32_t)(g1 - g0), bar);
+    }
+}
+
+template <int ESZ>
+__device__ void producer_loop(const KParams &KP, const SmemMap &S)
+{
+    const Params &P = KP.p;
+    const TaskDesc *tasks = P.tasks ? P.tasks : KP.inline_tasks;
+    const int32_t *gbeg = P.gbeg ? P.gbeg : KP.inline_gbeg;
+    const uint32_t lane = lane_id();
+    const uint32_t ring_off = (uint32_t)smem_ring_offset<ESZ>();
+    const uint32_t RING = (uint32_t)ring_bytes<ESZ>();
+    uint32_t *rbeg = S.range_beg(), *rend = S.range_end();
+    uint32_t head = 0;
+    int oldest = 0;
+    int i = 0;
+    bool failed = false;
+    for (;; ++i) {
+        const int g = sched_group(i, blockIdx.x, gridDim.x);
+        if (g >= P.ngroups)
+            break;
+        const int slot = i % kNumSlots;
+        const int t0 = gbeg[g];
+        const int nt = gbeg[g + 1] - t0;
+        if (nt < 0 || nt > kMaxGroupTasks) {
+            if (lane == 0)
+                set_error(P.err, kErrBadGroup);
+            failed = true;
+            break;
+        }
+        const bool has = (int)lane < nt;
+        TaskDesc d;
+        if (has)
+            d = tasks[t0 + lane];
+        else {
+            d.A = d.B = nullptr; d.C = nullptr;
+            d.lda = d.ldb = d.ldc = 1; d.M = d.N = d.K = 0; d.ta = d.tb = 0;
+            d.variant = 0; d.flags = 0; d.nbm = d.nbn = 1; d.alpha = d.beta = 0.0;
+        }
+        TaskStages st = plan_task(d, ESZ);
+        const uint32_t f = has ? st.total() : 0u;
+        const uint32_t tx = has ? (st.a.tx + st.b.tx + st.c.tx) : 0u;
+        const int nb = has ? (int)d.nbm * (int)d.nbn : 0;
+        uint32_t incl = f, txs = tx;
+        int nbi = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            int w = __shfl_up_sync(0xffffffffu, nbi, o);
+            if ((int)lane >= o) {
+                incl += v;
+                nbi += w;
+            }
+            txs += __shfl_xor_sync(0xffffffffu, txs, o);
+        }
+        const uint32_t F = __shfl_sync(0xffffffffu, incl, 31);
+        const int NB = __shfl_sync(0xffffffffu, nbi, 31);
+        const uint32_t excl = incl - f;
+
+        // claim ring space [a, a+F); wait until no live stage overlaps it
+        uint32_t a = 0;
+        int ok = 1;
+        if (lane == 0) {
+            a = (head + F <= RING) ? head : 0u;
+            int need = i - kNumSlots;   // the slot's previous user
+            for (int s = i - 1; s >= oldest && s > need; --s) {
+                const int ss = s % kNumSlots;
+                if (F > 0 && rbeg[ss] < a + F && a < rend[ss]) {
+                    need = s;
+                    break;
+                }
+            }
+            if (need >= oldest) {
+                ok = mbar_wait(S.empty(need % kNumSlots), (uint32_t)((need / kNumSlots) & 1), kWaitLimitNs);
+                oldest = need + 1;
+            }
+            rbeg[slot] = a;
+            rend[slot] = a + F;
+            head = a + F;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0)
+                set_error(P.err, kErrTimeoutEmpty);
+            failed = true;
+            break;
+        }
+        a = __shfl_sync(0xffffffffu, a, 0);
+
+        const uint32_t base = ring_off + a + excl;   // offset from the smem base
+        SlotHeader *hd = S.header(slot);
+        if (has) {
+            TaskRec r;
+            r.C = d.C;
+            r.ldc = d.ldc;
+            r.offA = (int32_t)(base + ((uint32_t)reinterpret_cast<uintptr_t>(d.A) & 15u));
+            r.offB = (int32_t)(base + st.a.bytes + ((uint32_t)reinterpret_cast<uintptr_t>(d.B) & 15u));
+            r.offC = (int32_t)(base + st.a.bytes + st.b.bytes + ((uint32_t)reinterpret_cast<uintptr_t>(d.C) & 15u));
+            r.csA = (int32_t)st.a.cs;
+            r.csB = (int32_t)st.b.cs;
+            r.csC = (int32_t)st.c.cs;
+            r.M = d.M; r.N = d.N; r.K = d.K;
+            r.ta = d.ta; r.tb = d.tb; r.variant = d.variant; r.flags = d.flags;
+            r.nbm = d.nbm; r.nbn = d.nbn;
+            r.alpha = d.alpha; r.beta = d.beta;
+            S.recs(slot)[lane] = r;
+        }
+        hd->prefix[lane] = has ? nbi : 0x7fffffff;
+        if (lane == 0) {
+            hd->ntasks = nt;
+            hd->nblocks = NB;
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive_expect_tx(S.full(slot), txs);
+        __syncwarp();
+        if (has) {
+            int ha, wa, hb, wb;
+            stored_dims(d, ha, wa, hb, wb);
+            const uint32_t bar = S.full(slot);
+            const uint32_t dst = S.sbase + base;
+            const bool prod = d.K > 0;
+            issue_stage(st.a, d.A, prod ? ha : 0, prod ? wa : 0, d.lda, ESZ, dst, bar);
+            issue_stage(st.b, d.B, prod ? hb : 0, prod ? wb : 0, d.ldb, ESZ, dst + st.a.bytes, bar);
+            issue_stage(st.c, d.C, d.M, d.N, d.ldc, ESZ, dst + st.a.bytes + st.b.bytes, bar);
+        }
+    }
+    // Copies still in flight target this CTA's shared memory: before leaving,
+    // wait (bounded) until every issued stage has landed.
+    if (lane == 0) {
+        const int first = i - kNumSlots > 0 ? i - kNumSlots : 0;
+        for (int s = first; s < i; ++s)
+            if (!mbar_wait(S.full(s % kNumSlots), (uint32_t)((s / kNumSlots) & 1), kWaitLimitNs))
+                set_error(P.err, kErrTimeoutFull);
+    }
+    (void)failed;
+}
+
+// Position of element m of canonical row kk: 16-byte groups XOR-swizzled by
+// the row so both re-pack directions and the tile loads avoid bank conflicts.
+template <int BM, int VE>
+__device__ __forceinline__ int swz(int m, int kk)
+{
+    constexpr int G0 = BM / VE;
+    constexpr int G = G0 >= 8 ? 8 : (G0 >= 1 ? G0 : 1);
+    return m ^ ((kk & (G - 1)) * VE);
+}
+
+// Re-pack one chunk of an operand into canonical rows X[kk][m], kk < kcp.
+// raw(m, kk) = src + m*sm + kk*sk.  Elements with m >= mh or kk >= kc are 0.
+// MFAST: lanes run along m (raw contiguous in m), else along kk.
+template <typename T, int BM, int KC, bool MFAST>
+__device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, int mh, int kc, int kcp)
+{
+    constexpr int VE = 16 / (int)sizeof(T);
+    const int lane = (int)lane_id();
+    if (MFAST) {
+        constexpr int STEP_ROWS = BM >= 32 ? 1 : 32 / BM;
+        constexpr int PER_ROW = BM >= 32 ? BM / 32 : 1;
+        const int m_l = BM >= 32 ? lane : (lane % BM);
+        const int kk_l = BM >= 32 ? 0 : (lane / BM);
+        for (int kk0 = 0; kk0 < kcp; kk0 += STEP_ROWS) {
+            const int kk = kk0 + kk_l;
+#pragma unroll
+            for (int q = 0; q < PER_ROW; ++q) {
+                const int m = m_l + 32 * q;
+                T v = T(0);
+                if (m < mh && kk < kc)
+                    v = *reinterpret_cast<const T *>(src + m * sm + kk * sk);
+                if (kk < kcp)
+                    X[kk * BM + swz<BM, VE>(m, kk)] = v;
+            }
+        }
+    } else {
+        constexpr int KL = KC;               // lanes along kk
+        constexpr int MSTEP = 32 / KL;       // m values per sweep
+        const int kk = lane % KL;
+        const int mo = lane / KL;
+        if (kk < kcp) {
+            const bool kin = kk < kc;
+            const char *s = src + kk * sk;
+            for (int m = mo; m < BM; m += MSTEP) {
+                T v = T(0);
+                if (kin && m < mh)
+                    v = *reinterpret_cast<const T *>(s + m * sm);
+                X[kk * BM + swz<BM, VE>(m, kk)] = v;
+            }
+        }
+    }
+}
+
+template <typename T, int MR, int NR, int LM, int LN>
+__device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, int bi, int bj, T *As, T *Bs)
+{
+    constexpr int ESZ = (int)sizeof(T);
+    constexpr int BM = LM * MR, BN = LN * NR;
+    constexpr int KC = Traits<ESZ>::KC;
+    constexpr int VE = 16 / ESZ;
+    const int lane = (int)lane_id();
+    const int M = r.M, N = r.N, K = r.K;
+    const int bh = (M + r.nbm - 1) / r.nbm;
+    const int bw = (N + r.nbn - 1) / r.nbn;
+    const int r0 = bi * bh, c0 = bj * bw;
+    const int mh = min(bh, M - r0), nw = min(bw, N - c0);
+    const int li = lane % LM, lj = lane / LM;
+
+    T acc[MR][NR];
+#pragma unroll
+    for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < NR; ++b)
+            acc[a][b] = T(0);
+
+    if (K > 0) {
+        const int am = r.ta ? r.csA : ESZ, ak = r.ta ? ESZ : r.csA;
+        const int bk = r.tb ? r.csB : ESZ, bn = r.tb ? ESZ : r.csB;
+        const char *Ab = smem + r.offA + r0 * am;
+        const char *Bb = smem + r.offB + c0 * bn;
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            const int kc = min(KC, K - k0);
+            const int kcp = (kc + 3) & ~3;
+            if (r.ta)
+                repack<T, BM, KC, false>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+            else
+                repack<T, BM, KC, true>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+            if (r.tb)
+                repack<T, BN, KC, true>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+            else
+                repack<T, BN, KC, false>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+            __syncwarp();
+            for (int kk0 = 0; kk0 < kcp; kk0 += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int kk = kk0 + u;
+                    const T *arow = As + kk * BM;
+                    const T *brow = Bs + kk * BN;
+                    T av[MR], bv[NR];
+                    if constexpr (MR >= VE) {
+#pragma unroll
+                        for (int q = 0; q < MR / VE; ++q) {
+                            const int pos = swz<BM, VE>(li * MR + q * VE, kk);
+                            if constexpr (ESZ == 4) {
+                                float4 t4 = *reinterpret_cast<const float4 *>(arow + pos);
+                                av[q * 4 + 0] = t4.x; av[q * 4 + 1] = t4.y;
+                                av[q * 4 + 2] = t4.z; av[q * 4 + 3] = t4.w;
+                            } else {
+                                double2 t2 = *reinterpret_cast<const double2 *>(arow + pos);
+                                av[q * 2 + 0] = t2.x; av[q * 2 + 1] = t2.y;
+                            }
+                        }
+                    } else {
+                        const int pos = swz<BM, VE>(li * MR, kk);
+#pragma unroll
+                        for (int q = 0; q < MR; ++q)
+                            av[q] = arow[pos + q];
+                    }
+                    if constexpr (NR >= VE) {
+#pragma unroll
+                        for (int q = 0; q < NR / VE; ++q) {
+                            const int pos = swz<BN, VE>(lj * NR + q * VE, kk);
+                            if constexpr (ESZ == 4) {
+                                float4 t4 = *reinterpret_cast<const float4 *>(brow + pos);
+                                bv[q * 4 + 0] = t4.x; bv[q * 4 + 1] = t4.y;
+                                bv[q * 4 + 2] = t4.z; bv[q * 4 + 3] = t4.w;
+                            } else {
+                                double2 t2 = *reinterpret_cast<const double2 *>(brow + pos);
+                                bv[q * 2 + 0] = t2.x; bv[q * 2 + 1] = t2.y;
+                            }
+                        }
+                    } else {
+                        const int pos = swz<BN, VE>(lj * NR, kk);
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+                            bv[q] = brow[pos + q];
+                    }
+#pragma unroll
+                    for (int a = 0; a < MR; ++a)
+#pragma unroll
+                        for (int b = 0; b < NR; ++b)
+                            acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+    // epilogue: C = alpha*acc + beta*C0, exact elements only
+    const T alpha = (T)r.alpha, beta = (T)r.beta;
+    const bool readc = (r.flags & kFlagReadC) != 0;
+    const char *Craw = smem + r.offC;
+    T *Cg = reinterpret_cast<T *>(r.C);
+    const int64_t ldc = r.ldc;
+#pragma unroll
+    for (int b = 0; b < NR; ++b) {
+        const int j = lj * NR + b;
+        if (j < nw) {
+            const int gj = c0 + j;
+#pragma unroll
+            for (int a = 0; a < MR; ++a) {
+                const int i = li * MR + a;
+                if (i < mh) {
+                    const int gi = r0 + i;
+                    T v = alpha * acc[a][b];
+                    if (readc)
+                        v = fma(beta, *reinterpret_cast<const T *>(Craw + gj * r.csC + gi * ESZ), v);
+                    Cg[gi + gj * ldc] = v;
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void dispatch_block(const char *smem, const TaskRec &r, int bi, int bj, T *As, T *Bs);
+
+template <>
+__device__ __forceinline__ void dispatch_block<float>(const char *smem, const TaskRec &r, int bi, int bj, float *As,
+                                                      float *Bs)
+{
+#define IAAT_V(id)                                                                                    \
+    case id:                                                                                          \
+        run_block<float, kVariantsF32[id].mr, kVariantsF32[id].nr, kVariantsF32[id].lm, kVariantsF32[id].ln>( \
+            smem, r, bi, bj, As, Bs);                                                                 \
+        break;
+    switch (r.variant) {
+        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4) IAAT_V(5)
+        IAAT_V(6) IAAT_V(7) IAAT_V(8) IAAT_V(9) IAAT_V(10) IAAT_V(11)
+    default:
+        break;
+    }
+#undef IAAT_V
+}
+
+template <>
+__device__ __forceinline__ void dispatch_block<double>(const char *smem, const TaskRec &r, int bi, int bj,
+                                                       double *As, double *Bs)
+{
+#define IAAT_V(id)                                                                                    \
+    case id:                                                                                          \
+        run_block<double, kVariantsF64[id].mr, kVariantsF64[id].nr, kVariantsF64[id].lm, kVariantsF64[id].ln>( \
+            smem, r, bi, bj, As, Bs);                                                                 \
+        break;
+    switch (r.variant) {
+        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4) IAAT_V(5)
+        IAAT_V(6) IAAT_V(7) IAAT_V(8) IAAT_V(9)
+    default:
+        break;
+    }
+#undef IAAT_V
+}
+
+template <typename T>
+__device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
+{
+    constexpr int ESZ = (int)sizeof(T);
+    const Params &P = KP.p;
+    const int lane = (int)lane_id();
+    T *As = reinterpret_cast<T *>(S.base + kSmemCanon + warp * Traits<ESZ>::kCanonBytes);
+    T *Bs = As + Traits<ESZ>::KC * kMaxBM;
+    for (int i = 0;; ++i) {
+        const int g = sched_group(i, blockIdx.x, gridDim.x);
+        if (g >= P.ngroups)
+            break;
+        const int slot = i % kNumSlots;
+        if (!mbar_wait(S.full(slot), (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs)) {
+            if (lane == 0)
+                set_error(P.err, kErrTimeoutFull);
+            return;
+        }
+        const SlotHeader *hd = S.header(slot);
+        const TaskRec *recs = S.recs(slot);
+        const int nb = hd->nblocks;
+        const int pre = hd->prefix[lane];
+        for (int b = warp; b < nb; b += kConsumerWarps) {
+            const int t = __popc(__ballot_sync(0xffffffffu, pre <= b));
+            const int before = __shfl_sync(0xffffffffu, pre, t > 0 ? t - 1 : 0);
+            const int lb = b - (t > 0 ? before : 0);
+            const TaskRec r = recs[t];
+            const int bi = lb % r.nbm, bj = lb / r.nbm;
+            dispatch_block<T>(S.base, r, bi, bj, As, Bs);
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(S.empty(slot));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_constant__ KParams KP)
+{
+    extern __shared__ __align__(128) char smem[];
+    SmemMap S;
+    S.base = smem;
+    S.sbase = smem_addr(smem);
+    const int warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kNumSlots; ++s) {
+            mbar_init(S.full(s), 1);
+            mbar_init(S.empty(s), kConsumerWarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == kConsumerWarps)
+        producer_loop<(int)sizeof(T)>(KP, S);
+    else
+        consumer_loop<T>(KP, S, warp);
+}
+
+}  // namespace iaat

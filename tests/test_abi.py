@@ -1,0 +1,93 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the
+header declares, and rejects bad arguments before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2208_09822_gb300 import build as B
+from paper_2208_09822_gb300 import iaat
+from paper_2208_09822_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return iaat.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "iaat.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(iaat_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert "iaat_gemm_grouped" in names and "iaat_plan_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version(L):
+    assert "sm_103a" in iaat.iaat_version()
+
+
+def _desc(**kw):
+    d = np.zeros(1, iaat.DESC_DTYPE)
+    base = dict(M=4, N=4, K=4, lda=4, ldb=4, ldc=4, transA=0, transB=0, alpha=1.0, beta=0.0,
+                A=0x10000, B=0x20000, C=0x30000)
+    base.update(kw)
+    for k, v in base.items():
+        d[k] = v
+    return d
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(M=-1), 1), (dict(lda=3), 1), (dict(ldb=3), 1), (dict(ldc=3), 1),
+    (dict(transA=2), 1), (dict(C=0), 1), (dict(A=0), 1),
+    (dict(M=80, N=80, K=81, lda=80, ldb=81, ldc=80), 2),                     # 518400 > 512000
+    (dict(M=32, N=32, K=33, transA=1, lda=33, ldb=33, ldc=32), 2),          # TN: 33792 > 32768
+    (dict(A=0x10002), 3), (dict(C=0x30001), 3),
+])
+def test_plan_create_rejects(L, kw, status):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(**kw), iaat.IAAT_F32)
+    assert e.value.status == status
+    assert "instance 0" in e.value.message
+
+
+def test_domain_boundary_is_inclusive(L):
+    """cbrt(MNK) <= 80 (Sec. I): 80^3 itself is small; TN's bound is 32^3."""
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "domain_bounds.txt"))
+            if l.strip() and not l.startswith("#")]
+    lim = {c: int(v) ** 3 for c, v in rows}
+    assert lim["NN"] == 512000 and lim["TN"] == 32768
+    assert W.in_domain(80, 80, 80, 0, 0) and not W.in_domain(80, 80, 81, 0, 0)
+    assert W.in_domain(32, 32, 32, 1, 0) and not W.in_domain(32, 32, 33, 1, 0)
+    assert W.in_domain(32, 32, 33, 1, 1)   # TT keeps the larger bound
+
+
+def test_fp64_rejects_tensor_precisions(L):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F64, iaat.IAAT_PREC_3XBF16)
+    assert e.value.status == 4
+
+
+def test_single_call_rejects(L):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_sgemm(0, 0, 81, 80, 80, 1.0, 0x1000, 81, 0x2000, 80, 0.0, 0x3000, 81)
+    assert e.value.status == 2
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_dgemm(0, 0, 4, 4, 4, 1.0, 0x1004, 4, 0x2000, 4, 0.0, 0x3000, 4)
+    assert e.value.status == 3
+
+
+def test_quick_returns_touch_nothing(L):
+    # M == 0 / N == 0 is a no-op with any pointers; alpha == 0 with beta == 1 too
+    iaat.iaat_sgemm(0, 0, 0, 5, 5, 1.0, 0, 1, 0, 5, 0.0, 0, 1)
+    iaat.iaat_sgemm(0, 0, 5, 0, 5, 1.0, 0, 5, 0, 5, 0.0, 0, 5)
+    iaat.iaat_sgemm(0, 0, 5, 5, 5, 0.0, 0, 5, 0, 5, 1.0, 0x3000, 5)
