@@ -149,51 +149,39 @@ struct Variant {
 };
 
 // FP32 family.
-constexpr int kNumVariantsF32 = 12;
+constexpr int kNumVariantsF32 = 5;
 constexpr Variant kVariantsF32[kNumVariantsF32] = {
     {4, 8, 8, 4},   // 0: 32 x 32
     {4, 4, 8, 4},   // 1: 32 x 16
     {4, 4, 4, 8},   // 2: 16 x 32
     {2, 4, 8, 4},   // 3: 16 x 16
-    {2, 2, 8, 4},   // 4: 16 x 8
-    {2, 2, 4, 8},   // 5: 8 x 16
-    {1, 2, 8, 4},   // 6: 8 x 8
-    {1, 1, 8, 4},   // 7: 8 x 4
-    {1, 1, 4, 8},   // 8: 4 x 8
-    {1, 1, 32, 1},  // 9: 32 x 1
-    {1, 1, 1, 32},  // 10: 1 x 32
-    {8, 8, 4, 8},   // 11: 32 x 64
+    {1, 2, 8, 4},   // 4: 8 x 8
 };
 
 // FP64 family (DFMA; each accumulator takes two registers).
-constexpr int kNumVariantsF64 = 10;
+constexpr int kNumVariantsF64 = 5;
 constexpr Variant kVariantsF64[kNumVariantsF64] = {
     {4, 8, 8, 4},   // 0: 32 x 32
     {4, 4, 8, 4},   // 1: 32 x 16
     {4, 4, 4, 8},   // 2: 16 x 32
     {2, 4, 8, 4},   // 3: 16 x 16
-    {2, 2, 8, 4},   // 4: 16 x 8
-    {2, 2, 4, 8},   // 5: 8 x 16
-    {1, 1, 8, 4},   // 6: 8 x 4
-    {1, 1, 4, 8},   // 7: 4 x 8
-    {1, 1, 32, 1},  // 8: 32 x 1
-    {1, 1, 1, 32},  // 9: 1 x 32
+    {1, 2, 8, 4},   // 4: 8 x 8
 };
 
 // K is consumed in chunks of kKC (FP32) / kKC64 (FP64) staged per warp.
 constexpr int kKC = 16;
 constexpr int kKC64 = 8;
-constexpr int kMaxBM = 32, kMaxBN = 64;  // largest warp block over both families
+constexpr int kMaxBM = 32, kMaxBN = 32;  // largest warp block over both families
 
 // Per-warp canonical operand buffers: As[KC][BM], Bs[KC][BN].
 template <int ESZ> struct Traits;
 template <> struct Traits<4> {
     static constexpr int KC = kKC;
-    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 4;   // 6 KB
+    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 4;   // 4 KB
 };
 template <> struct Traits<8> {
     static constexpr int KC = kKC64;
-    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 8;   // 6 KB
+    static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 8;   // 4 KB
 };
 
 // Shared-memory map of the persistent kernel (byte offsets).

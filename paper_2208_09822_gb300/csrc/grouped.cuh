@@ -36,6 +36,8 @@ __device__ __forceinline__ void set_error(int32_t *err, int32_t code)
 struct SmemMap {
     char *base;
     uint32_t sbase;
+    uint32_t ring_off;     // byte offset of the staging ring from base
+    uint32_t ring_bytes;   // its size
     __device__ uint32_t full(int s) const { return sbase + kSmemBarriers + 8 * s; }
     __device__ uint32_t empty(int s) const { return sbase + kSmemBarriers + 64 + 8 * s; }
     __device__ uint32_t *range_beg() const { return reinterpret_cast<uint32_t *>(base + 128); }
@@ -78,8 +80,8 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
     const TaskDesc *tasks = P.tasks ? P.tasks : KP.inline_tasks;
     const int32_t *gbeg = P.gbeg ? P.gbeg : KP.inline_gbeg;
     const uint32_t lane = lane_id();
-    const uint32_t ring_off = (uint32_t)smem_ring_offset<ESZ>();
-    const uint32_t RING = (uint32_t)ring_bytes<ESZ>();
+    const uint32_t ring_off = S.ring_off;
+    const uint32_t RING = S.ring_bytes;
     uint32_t *rbeg = S.range_beg(), *rend = S.range_end();
     uint32_t head = 0;
     int oldest = 0;
@@ -220,7 +222,7 @@ __device__ __forceinline__ int swz(int m, int kk)
 // raw(m, kk) = src + m*sm + kk*sk.  Elements with m >= mh or kk >= kc are 0.
 // MFAST: lanes run along m (raw contiguous in m), else along kk.
 template <typename T, int BM, int KC, bool MFAST>
-__device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, int mh, int kc, int kcp)
+__device__ __noinline__ void repack(T *X, const char *src, int sm, int sk, int mh, int kc, int kcp)
 {
     constexpr int VE = 16 / (int)sizeof(T);
     const int lane = (int)lane_id();
@@ -229,6 +231,7 @@ __device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, in
         constexpr int PER_ROW = BM >= 32 ? BM / 32 : 1;
         const int m_l = BM >= 32 ? lane : (lane % BM);
         const int kk_l = BM >= 32 ? 0 : (lane / BM);
+#pragma unroll 1
         for (int kk0 = 0; kk0 < kcp; kk0 += STEP_ROWS) {
             const int kk = kk0 + kk_l;
 #pragma unroll
@@ -249,6 +252,7 @@ __device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, in
         if (kk < kcp) {
             const bool kin = kk < kc;
             const char *s = src + kk * sk;
+#pragma unroll 4
             for (int m = mo; m < BM; m += MSTEP) {
                 T v = T(0);
                 if (kin && m < mh)
@@ -286,6 +290,7 @@ __device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, in
         const int bk = r.tb ? r.csB : ESZ, bn = r.tb ? ESZ : r.csB;
         const char *Ab = smem + r.offA + r0 * am;
         const char *Bb = smem + r.offB + c0 * bn;
+#pragma unroll 1
         for (int k0 = 0; k0 < K; k0 += KC) {
             const int kc = min(KC, K - k0);
             const int kcp = (kc + 3) & ~3;
@@ -298,6 +303,7 @@ __device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, in
             else
                 repack<T, BN, KC, false>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
             __syncwarp();
+#pragma unroll 1
             for (int kk0 = 0; kk0 < kcp; kk0 += 4) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -393,8 +399,7 @@ __device__ __forceinline__ void dispatch_block<float>(const char *smem, const Ta
             smem, r, bi, bj, As, Bs);                                                                 \
         break;
     switch (r.variant) {
-        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4) IAAT_V(5)
-        IAAT_V(6) IAAT_V(7) IAAT_V(8) IAAT_V(9) IAAT_V(10) IAAT_V(11)
+        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4)
     default:
         break;
     }
@@ -411,8 +416,7 @@ __device__ __forceinline__ void dispatch_block<double>(const char *smem, const T
             smem, r, bi, bj, As, Bs);                                                                 \
         break;
     switch (r.variant) {
-        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4) IAAT_V(5)
-        IAAT_V(6) IAAT_V(7) IAAT_V(8) IAAT_V(9)
+        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4)
     default:
         break;
     }
@@ -462,6 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
     SmemMap S;
     S.base = smem;
     S.sbase = smem_addr(smem);
+    S.ring_off = (uint32_t)smem_ring_offset<(int)sizeof(T)>();
+    S.ring_bytes = (uint32_t)ring_bytes<(int)sizeof(T)>();
     const int warp = threadIdx.x / 32;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNumSlots; ++s) {

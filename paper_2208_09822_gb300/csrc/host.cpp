@@ -89,7 +89,15 @@ static const Variant *variants(int esz, int *n)
     return kVariantsF64;
 }
 
-static double block_cost(const Variant &v, int esz, int K)
+namespace iaat {
+// The tiler's cost model without the tuned per-variant scale (the
+// autotuner calibrates against it).
+double model_block_cost(const Variant &v, int esz, int K);
+}
+
+static double block_cost(const Variant &v, int esz, int K) { return iaat::model_block_cost(v, esz, K); }
+
+double iaat::model_block_cost(const Variant &v, int esz, int K)
 {
     const int ve = 16 / esz;
     const int kc = esz == 4 ? kKC : kKC64;
@@ -239,21 +247,24 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][2];
+bool g_prepared[64][5];
 
-iaat_status_t prepare_device(int dev, int dtype)
+// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2.. = tcgen05 precision (kind - 1)
+iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
     if (dev < 0 || dev >= 64)
         return fail(IAAT_ERR_CUDA, "device index %d out of range", dev);
-    if (!g_prepared[dev][dtype]) {
-        cudaError_t e = prepare_fma(dtype);
+    if (!g_prepared[dev][kind]) {
+        cudaError_t e = kind < 2 ? prepare_fma(kind) : prepare_tc(kind - 1);
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaFuncSetAttribute");
-        g_prepared[dev][dtype] = true;
+        g_prepared[dev][kind] = true;
     }
     return IAAT_OK;
 }
+
+int kernel_kind(int esz, iaat_precision_t prec) { return prec != IAAT_PREC_DEFAULT ? 1 + (int)prec : (esz == 4 ? 0 : 1); }
 
 int g_sm_count[64];
 
@@ -271,7 +282,7 @@ int sm_count(int dev)
 
 // Build the tasks of one instance (one, or several column pieces when its
 // operands do not fit one stage).
-iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int force_variant,
+iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int force_variant, uint32_t cap,
                          std::vector<HostTask> &out, int64_t *blocks_out)
 {
     const int M = g.M, N = g.N;
@@ -280,7 +291,6 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int fo
     const int Keff = (g.alpha == 0.0) ? 0 : g.K;
     if (Keff == 0 && g.beta == 1.0)
         return IAAT_OK;   // C = 1*C: nothing to do
-    const uint32_t cap = (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
     for (int pieces = 1; pieces <= N; ++pieces) {
         const int width = (N + pieces - 1) / pieces;
         const int np = (N + width - 1) / width;
@@ -335,12 +345,11 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int fo
 
 // Order tasks by cost (largest first) and cut them into stages of at most
 // max_tasks tasks and max_group_bytes of shared memory.
-void make_groups(std::vector<HostTask> &tasks, int esz, int max_tasks, std::vector<TaskDesc> &flat,
+void make_groups(std::vector<HostTask> &tasks, uint32_t cap, int max_tasks, std::vector<TaskDesc> &flat,
                  std::vector<int32_t> &gbeg)
 {
     std::stable_sort(tasks.begin(), tasks.end(),
                      [](const HostTask &a, const HostTask &b) { return a.cost > b.cost; });
-    const uint32_t cap = (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
     flat.clear();
     gbeg.clear();
     uint32_t used = 0;
@@ -356,6 +365,34 @@ void make_groups(std::vector<HostTask> &tasks, int esz, int max_tasks, std::vect
         ++count;
     }
     gbeg.push_back((int32_t)flat.size());
+}
+
+// tcgen05 plans: inside each stage, order the tasks by K (largest first) and
+// stack them into packs of at most 128 rows and 128 columns (one MMA tile
+// each).  A task's pack index, row offset and column offset travel in its
+// variant / nbm / nbn fields.  Returns the number of packs.
+int64_t make_packs(std::vector<TaskDesc> &flat, const std::vector<int32_t> &gbeg)
+{
+    int64_t npacks = 0;
+    for (size_t g = 0; g + 1 < gbeg.size(); ++g) {
+        auto b = flat.begin() + gbeg[g], e = flat.begin() + gbeg[g + 1];
+        std::stable_sort(b, e, [](const TaskDesc &x, const TaskDesc &y) { return x.K > y.K; });
+        int pack = 0, rows = 0, cols = 0;
+        for (auto it = b; it != e; ++it) {
+            if (rows > 0 && (rows + it->M > kTcPackRows || cols + it->N > kTcPackCols)) {
+                ++pack;
+                rows = 0;
+                cols = 0;
+            }
+            it->variant = (uint8_t)pack;
+            it->nbm = (uint8_t)rows;
+            it->nbn = (uint8_t)cols;
+            rows += it->M;
+            cols += it->N;
+        }
+        npacks += pack + 1;
+    }
+    return npacks;
 }
 
 }  // namespace
@@ -375,10 +412,16 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         return fail(IAAT_ERR_INVALID_VALUE, "unknown precision %d", (int)precision);
     if (precision != IAAT_PREC_DEFAULT && dtype == IAAT_F64)
         return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");
-    if (precision != IAAT_PREC_DEFAULT)
-        return fail(IAAT_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library yet");
     const int esz = dtype == IAAT_F32 ? 4 : 8;
+    const bool tc = precision != IAAT_PREC_DEFAULT;
+    const uint32_t cap = tc ? (uint32_t)tc_group_cap((int)precision)
+                            : (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
     int max_tasks = kMaxGroupTasks;
+    {
+        const int tuned = dtype == IAAT_F64 ? tuning().group_tasks_f64 : tuning().group_tasks[(int)precision];
+        if (tuned > 0)
+            max_tasks = tuned;
+    }
     int force_variant = -1;
     int ctas_per_sm = 1;
     if (opts) {
@@ -410,7 +453,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         if (st != IAAT_OK)
             return st;
         const size_t before = tasks.size();
-        st = make_tasks(i, g, esz, force_variant, tasks, &nblocks);
+        st = make_tasks(i, g, esz, force_variant, cap, tasks, &nblocks);
         if (st != IAAT_OK)
             return st;
         if (tasks.size() > before) {
@@ -422,7 +465,9 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     }
     std::vector<TaskDesc> flat;
     std::vector<int32_t> gbeg;
-    make_groups(tasks, esz, max_tasks, flat, gbeg);
+    make_groups(tasks, cap, max_tasks, flat, gbeg);
+    if (tc)
+        nblocks = make_packs(flat, gbeg);
     if (opts && opts->inject_fault == 1 && gbeg.size() >= 2)
         gbeg[1] = gbeg[0] + kMaxGroupTasks + 1;   // a stage the kernel must reject
 
@@ -434,7 +479,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         delete plan;
         return cuda_fail(e, "cudaGetDevice");
     }
-    iaat_status_t ps = prepare_device(plan->device, dtype == IAAT_F32 ? 0 : 1);
+    iaat_status_t ps = prepare_device(plan->device, kernel_kind(esz, precision));
     if (ps != IAAT_OK) {
         delete plan;
         return ps;
@@ -486,7 +531,9 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
     kp.p.gbeg = plan->d_gbeg;
     kp.p.ngroups = (int32_t)plan->ngroups;
     kp.p.err = plan->d_err;
-    cudaError_t e = launch_fma(plan->esz == 4 ? 0 : 1, kp, plan->grid, static_cast<cudaStream_t>(stream));
+    cudaError_t e = plan->precision != IAAT_PREC_DEFAULT
+                        ? launch_tc((int)plan->precision, kp, plan->grid, static_cast<cudaStream_t>(stream))
+                        : launch_fma(plan->esz == 4 ? 0 : 1, kp, plan->grid, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return cuda_fail(e, "kernel launch");
     return IAAT_OK;
@@ -562,7 +609,7 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     iaat_gemm_desc_t g{M, N, K, lda, ldb, ldc, ta, tb, alpha, beta, A, B, C};
     std::vector<HostTask> tasks;
     int64_t nb = 0;
-    st = make_tasks(0, g, esz, -1, tasks, &nb);
+    st = make_tasks(0, g, esz, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks, &nb);
     if (st != IAAT_OK)
         return st;
     if (tasks.empty())
@@ -573,7 +620,7 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaGetDevice");
-    st = prepare_device(dev, esz == 4 ? 0 : 1);
+    st = prepare_device(dev, kernel_kind(esz, IAAT_PREC_DEFAULT));
     if (st != IAAT_OK)
         return st;
     KParams kp;

@@ -7,4 +7,10 @@ namespace iaat {
 cudaError_t prepare_fma(int dtype);
 cudaError_t launch_fma(int dtype, const KParams &kp, int grid, cudaStream_t stream);
 cudaError_t single_call_err_ptr(int32_t **p);
+// tcgen05 kernel, precision 1 = 3xBF16, 2 = TF32, 3 = FP16 (iaat_precision_t)
+cudaError_t prepare_tc(int precision);
+cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t stream);
+int tc_group_cap(int precision);        // largest stage footprint (bytes)
+constexpr int kTcPackRows = 128;        // rows of one MMA tile
+constexpr int kTcPackCols = 128;        // columns of one MMA tile
 }  // namespace iaat

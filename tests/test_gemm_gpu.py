@@ -142,7 +142,7 @@ def test_large_leading_dimensions(dtype):
     _assert_ok(b, C, compare(b, C), TOL[dtype])
 
 
-@pytest.mark.parametrize("variant", range(1, 13))
+@pytest.mark.parametrize("variant", range(1, 6))
 def test_every_fp32_variant(variant):
     b = W.random_small(600, seed=100 + variant, dtype=np.float32, max_dim=70, pad_max=4, misalign_max=3)
     b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])
@@ -150,7 +150,7 @@ def test_every_fp32_variant(variant):
     _assert_ok(b, C, compare(b, C), 1e-5)
 
 
-@pytest.mark.parametrize("variant", range(1, 11))
+@pytest.mark.parametrize("variant", range(1, 6))
 def test_every_fp64_variant(variant):
     b = W.random_small(400, seed=200 + variant, dtype=np.float64, max_dim=70, pad_max=4, misalign_max=1)
     b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])

@@ -45,10 +45,11 @@ def test_gpu_tiling_is_an_exact_cover(dtype):
 
 
 def test_gpu_tiling_blocks_fit_a_variant():
-    # every block of the FP32 tiler is at most 32 x 64
-    for M, N in itertools.product(range(1, 81, 7), range(1, 81, 5)):
-        for r, c, m, n in iaat.iaat_tile(iaat.IAAT_F32, 0, 0, M, N, 16):
-            assert m <= 32 and n <= 64
+    # every block of the tilers is at most 32 x 32
+    for dt in (iaat.IAAT_F32, iaat.IAAT_F64):
+        for M, N in itertools.product(range(1, 81, 7), range(1, 81, 5)):
+            for r, c, m, n in iaat.iaat_tile(dt, 0, 0, M, N, 16):
+                assert m <= 32 and n <= 32
 
 
 def test_exact_tiler_worked_example(golden_dir):
