@@ -162,6 +162,11 @@ iaat_status_t iaat_plan_destroy(iaat_plan_t plan);
 iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t precision,
                             const char *cache_path);
 
+/* Measure the FP32 FFMA (IAAT_F32) or FP64 DFMA (IAAT_F64) pipe throughput
+ * of the current GPU in GFLOP/s (2 flops per FMA), the compute roof of the
+ * CUDA-core paths.  Synchronous; allocates a small scratch buffer. */
+iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops);
+
 /* Host-only view of the run-time tiler (no GPU needed).  Tiles one M x N
  * (x K) instance of the given type and case with the library's register-tile
  * variants and writes up to `cap` blocks as (row0, col0, rows, cols)

@@ -655,3 +655,13 @@ extern "C" iaat_status_t iaat_dgemm(int transA, int transB, int M, int N, int K,
 {
     return single_gemm(8, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
 }
+
+extern "C" iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops)
+{
+    if ((dtype != IAAT_F32 && dtype != IAAT_F64) || !gflops)
+        return fail(IAAT_ERR_INVALID_VALUE, "bad argument");
+    cudaError_t e = measure_fma_peak(dtype == IAAT_F32 ? 0 : 1, gflops);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "FMA peak probe");
+    return IAAT_OK;
+}

@@ -7,6 +7,7 @@ namespace iaat {
 cudaError_t prepare_fma(int dtype);
 cudaError_t launch_fma(int dtype, const KParams &kp, int grid, cudaStream_t stream);
 cudaError_t single_call_err_ptr(int32_t **p);
+cudaError_t measure_fma_peak(int dtype, double *gflops);   // 0 FP32 FFMA, 1 FP64 DFMA
 // tcgen05 kernel, precision 1 = 3xBF16, 2 = TF32, 3 = FP16 (iaat_precision_t)
 cudaError_t prepare_tc(int precision);
 cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t stream);

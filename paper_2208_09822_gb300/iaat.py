@@ -78,6 +78,8 @@ def lib():
         L.iaat_plan_destroy.argtypes = [P]
         L.iaat_autotune.restype = S
         L.iaat_autotune.argtypes = [I, I, ctypes.c_char_p]
+        L.iaat_fma_peak.restype = S
+        L.iaat_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
         L.iaat_tile.restype = ctypes.c_int64
         L.iaat_tile.argtypes = [I, I, I, I, I, I, P, ctypes.c_int64]
         L.iaat_tile_exact.restype = ctypes.c_int64
@@ -169,6 +171,13 @@ def iaat_plan_destroy(plan):
 
 def iaat_autotune(dtype, precision=IAAT_PREC_DEFAULT, cache_path=None):
     _check(lib().iaat_autotune(dtype, precision, cache_path.encode() if cache_path else None))
+
+
+def iaat_fma_peak(dtype):
+    """FMA-pipe throughput of the current GPU in GFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().iaat_fma_peak(dtype, ctypes.byref(v)))
+    return v.value
 
 
 def iaat_tile(dtype, transA, transB, M, N, K):
