@@ -129,6 +129,30 @@ iaat_status_t iaat_dgemm(int transA, int transB, int M, int N, int K,
                          const double *B, int ldb, double beta, double *C,
                          int ldc, void *stream);
 
+/* Allocation-free grouped GEMM.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory after start-up
+ * -- for example a serving process that reserves all GPU memory at launch and
+ * treats any later cudaMalloc as a failure, because cudaMalloc/cudaFree
+ * synchronise the device and can fail under memory pressure.
+ *
+ * Same arguments and results as iaat_plan_create + iaat_gemm_grouped with the
+ * default precision, but nothing is allocated on the device or the heap: the
+ * plan is built in static host arrays, copied with cudaMemcpyAsync on
+ * `stream` into one fixed device scratch array of about 545 KB (a file-scope
+ * __device__ array that every GPU loading this library holds until the
+ * process exits), and the CUDA-core grouped kernel runs from there.
+ * Limits: at most 8192 tasks per call (an instance is one task, or a few
+ * column pieces when its operands do not fit one pipeline stage); larger
+ * batches return IAAT_ERR_INVALID_VALUE and enqueue nothing.
+ * The first call on a device looks up the scratch array's device address
+ * (and reads the tuning cache); make that first call before any stream
+ * capture.  Every call reuses the same scratch array and the kernel reads it
+ * while it runs, so calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results: order them on one stream.  A device
+ * time-out is reported by iaat_plan_check(NULL, stream). */
+iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t count,
+                                        iaat_dtype_t dtype, void *stream);
+
 /* Build a plan for `count` instances (host array `descs`, device pointers
  * inside): validates every instance (the first failure's index is in
  * iaat_last_error), tiles each one into warp blocks (run-time stage,

@@ -22,16 +22,14 @@ using namespace iaat;
 
 // ------------------------------------------------------------- errors
 
-static thread_local std::string g_last_error;
+static thread_local char g_last_error[512];
 
 static iaat_status_t fail(iaat_status_t st, const char *fmt, ...)
 {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
     va_end(ap);
-    g_last_error = buf;
     return st;
 }
 
@@ -40,7 +38,7 @@ static iaat_status_t cuda_fail(cudaError_t e, const char *what)
     return fail(IAAT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-extern "C" const char *iaat_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *iaat_last_error(void) { return g_last_error; }
 
 extern "C" const char *iaat_version(void) { return "iaat-gb300 0.1 (sm_103a)"; }
 
@@ -565,6 +563,14 @@ extern "C" iaat_status_t iaat_plan_check(iaat_plan_t plan, void *stream)
         cudaError_t e = single_call_err_ptr(&w);
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress");
+        int32_t *w2 = nullptr;
+        if ((e = noalloc_err_ptr(&w2)) != cudaSuccess)
+            return cuda_fail(e, "cudaGetDevice");
+        if (w2) {
+            const iaat_status_t st = read_and_clear(w2, static_cast<cudaStream_t>(stream));
+            if (st != IAAT_OK)
+                return st;
+        }
     }
     return read_and_clear(w, static_cast<cudaStream_t>(stream));
 }
@@ -665,3 +671,117 @@ extern "C" iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops)
         return cuda_fail(e, "FMA peak probe");
     return IAAT_OK;
 }
+
+// ------------------------------------------- allocation-free planning
+// The planning of iaat_plan_create, written into fixed arrays supplied by
+// the caller instead of growing containers, for the entry point that must
+// not allocate (iaat_gemm_grouped_noalloc).  Same validation, tiling,
+// column splitting, ordering and stage cutting as the regular planner.
+iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, int esz, int max_tasks,
+                                 TaskDesc *tasks, uint32_t *bytes, double *cost, int32_t *order, TaskDesc *out,
+                                 int32_t *gbeg, int64_t *ntasks_out, int64_t *ngroups_out)
+{
+    const uint32_t cap = (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
+    int64_t nt = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        iaat_status_t st = check_instance(i, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+                                          g.alpha, esz);
+        if (st != IAAT_OK)
+            return st;
+        const int M = g.M, N = g.N;
+        if (M == 0 || N == 0)
+            continue;
+        const int Keff = (g.alpha == 0.0) ? 0 : g.K;
+        if (Keff == 0 && g.beta == 1.0)
+            continue;
+        bool placed = false;
+        for (int pieces = 1; pieces <= N && !placed; ++pieces) {
+            const int width = (N + pieces - 1) / pieces;
+            const int np = (N + width - 1) / width;
+            if (nt + np > max_tasks)
+                return fail(IAAT_ERR_INVALID_VALUE,
+                            "instance %lld: the batch needs more than %d tasks, the limit of the allocation-free "
+                            "entry point", (long long)i, max_tasks);
+            bool fits = true;
+            for (int p = 0; p < np && fits; ++p) {
+                const int c0 = p * width;
+                const int nw = std::min(width, N - c0);
+                TaskDesc d{};
+                d.A = static_cast<const char *>(g.A);
+                d.B = g.B ? static_cast<const char *>(g.B) +
+                                (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * esz
+                          : nullptr;
+                d.C = static_cast<char *>(g.C) + (size_t)((int64_t)c0 * g.ldc) * esz;
+                d.lda = g.lda;
+                d.ldb = g.ldb;
+                d.ldc = g.ldc;
+                d.M = (int16_t)M;
+                d.N = (int16_t)nw;
+                d.K = (int16_t)Keff;
+                d.ta = (uint8_t)g.transA;
+                d.tb = (uint8_t)g.transB;
+                d.flags = (g.beta != 0.0) ? kFlagReadC : 0;
+                d.alpha = esz == 4 ? (double)(float)g.alpha : g.alpha;
+                d.beta = esz == 4 ? (double)(float)g.beta : g.beta;
+                const TileChoice t = choose_tiling(esz, M, nw, Keff, -1);
+                d.variant = (uint8_t)t.variant;
+                d.nbm = (uint8_t)t.nbm;
+                d.nbn = (uint8_t)t.nbn;
+                const TaskStages sg = plan_task(d, esz);
+                if (sg.total() > cap) {
+                    fits = false;
+                    break;
+                }
+                tasks[nt + p] = d;
+                bytes[nt + p] = sg.total();
+                cost[nt + p] = (double)(sg.a.tx + sg.b.tx + sg.c.tx) + tuning().cost_per_slot * t.cost;
+            }
+            if (fits) {
+                nt += np;
+                placed = true;
+            }
+        }
+        if (!placed)
+            return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage", (long long)i);
+    }
+    // largest cost first, ties in input order (the regular planner's stable order)
+    for (int64_t k = 0; k < nt; ++k)
+        order[k] = (int32_t)k;
+    std::sort(order, order + nt, [cost](int32_t a, int32_t b) {
+        return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
+    });
+    int group_tasks = kMaxGroupTasks;
+    {
+        const int tuned = esz == 8 ? tuning().group_tasks_f64 : tuning().group_tasks[0];
+        if (tuned > 0)
+            group_tasks = tuned;
+    }
+    int64_t ng = 0;
+    uint32_t used = 0;
+    int in_group = 0;
+    for (int64_t k = 0; k < nt; ++k) {
+        const int32_t t = order[k];
+        if (in_group == 0 || in_group >= group_tasks || used + bytes[t] > cap) {
+            gbeg[ng++] = (int32_t)k;
+            used = 0;
+            in_group = 0;
+        }
+        out[k] = tasks[t];
+        used += bytes[t];
+        ++in_group;
+    }
+    gbeg[ng] = (int32_t)nt;
+    *ntasks_out = nt;
+    *ngroups_out = ng;
+    return IAAT_OK;
+}
+
+iaat_status_t iaat::noalloc_fail(iaat_status_t st, const char *msg) { return fail(st, "%s", msg); }
+
+iaat_status_t iaat::noalloc_prepare(int dev)
+{
+    return prepare_device(dev, 0) == IAAT_OK && prepare_device(dev, 1) == IAAT_OK ? IAAT_OK : IAAT_ERR_CUDA;
+}
+
+int iaat::noalloc_sm_count(int dev) { return sm_count(dev); }

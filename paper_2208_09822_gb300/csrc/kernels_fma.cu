@@ -1,5 +1,8 @@
 // Instantiations and launchers of the CUDA-core grouped kernel.
 #include <cuda_runtime.h>
+
+#include <mutex>
+
 #include "grouped.cuh"
 #include "launch.h"
 
@@ -97,3 +100,99 @@ cudaError_t measure_fma_peak(int dtype, double *gflops)
 }
 
 }  // namespace iaat
+
+// ------------------------------------------------ allocation-free entry
+// Scratch of iaat_gemm_grouped_noalloc: the error word, the stage index and
+// the task descriptors of one call, in a fixed array that every GPU loading
+// this library holds until the process exits (about 545 KB).
+namespace iaat {
+constexpr int kNoAllocMaxTasks = 8192;
+constexpr size_t kNoAllocGbegOff = 256;
+constexpr size_t kNoAllocTasksOff = kNoAllocGbegOff + (((kNoAllocMaxTasks + 1) * sizeof(int32_t) + 255) & ~(size_t)255);
+constexpr size_t kNoAllocBytes = kNoAllocTasksOff + (size_t)kNoAllocMaxTasks * sizeof(TaskDesc);
+}  // namespace iaat
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[iaat::kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;          // guards the host staging arrays below
+char *g_noalloc_dev[64];             // device address of the scratch, per device (set-up)
+iaat::TaskDesc g_na_tasks[iaat::kNoAllocMaxTasks];
+iaat::TaskDesc g_na_sorted[iaat::kNoAllocMaxTasks];
+uint32_t g_na_bytes[iaat::kNoAllocMaxTasks];
+double g_na_cost[iaat::kNoAllocMaxTasks];
+int32_t g_na_order[iaat::kNoAllocMaxTasks];
+int32_t g_na_gbeg[iaat::kNoAllocMaxTasks + 1];
+}  // namespace
+
+// See include/iaat.h.  Host planning goes into the static arrays above; the
+// result is copied into g_noalloc_scratch on the caller's stream and the
+// CUDA-core grouped kernel runs from there.
+extern "C" iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t count, iaat_dtype_t dtype,
+                                                   void *stream)
+{
+    using namespace iaat;
+    if (count < 0 || (count > 0 && !descs))
+        return noalloc_fail(IAAT_ERR_INVALID_VALUE, "bad descriptor array");
+    if (dtype != IAAT_F32 && dtype != IAAT_F64)
+        return noalloc_fail(IAAT_ERR_INVALID_VALUE, "unknown dtype");
+    if (count > kNoAllocMaxTasks)
+        return noalloc_fail(IAAT_ERR_INVALID_VALUE,
+                            "more than 8192 instances: the allocation-free entry point holds at most 8192 tasks");
+    const int esz = dtype == IAAT_F32 ? 4 : 8;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return noalloc_fail(IAAT_ERR_CUDA, "cudaGetDevice failed");
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_dev[dev]) {
+        // set-up, once per device, with that device current
+        char *ptr = nullptr;
+        if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+            return noalloc_fail(IAAT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+        if (noalloc_prepare(dev) != IAAT_OK)
+            return noalloc_fail(IAAT_ERR_CUDA, "kernel attribute set-up failed");
+        g_noalloc_dev[dev] = ptr;
+    }
+    char *scratch = g_noalloc_dev[dev];
+    int64_t nt = 0, ng = 0;
+    iaat_status_t st = noalloc_plan(descs, count, esz, kNoAllocMaxTasks, g_na_tasks, g_na_bytes, g_na_cost,
+                                    g_na_order, g_na_sorted, g_na_gbeg, &nt, &ng);
+    if (st != IAAT_OK)
+        return st;
+    if (ng == 0)
+        return IAAT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The host arrays are pageable, so each copy has taken its data when it
+    // returns; the arrays can be reused by the next call at once.
+    if (cudaMemsetAsync(scratch, 0, sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemcpyAsync(scratch + kNoAllocGbegOff, g_na_gbeg, (size_t)(ng + 1) * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(scratch + kNoAllocTasksOff, g_na_sorted, (size_t)nt * sizeof(TaskDesc),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return noalloc_fail(IAAT_ERR_CUDA, "copy into the scratch array failed");
+    KParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.p.tasks = reinterpret_cast<const TaskDesc *>(scratch + kNoAllocTasksOff);
+    kp.p.gbeg = reinterpret_cast<const int32_t *>(scratch + kNoAllocGbegOff);
+    kp.p.ngroups = (int32_t)ng;
+    kp.p.err = reinterpret_cast<int32_t *>(scratch);
+    const int grid = (int)(ng < noalloc_sm_count(dev) ? ng : noalloc_sm_count(dev));
+    if (launch_fma(esz == 4 ? 0 : 1, kp, grid, s) != cudaSuccess)
+        return noalloc_fail(IAAT_ERR_CUDA, "kernel launch failed");
+    return IAAT_OK;
+}
+
+// Error word of the allocation-free entry point (for iaat_plan_check(NULL)).
+cudaError_t iaat::noalloc_err_ptr(int32_t **p)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64 && g_noalloc_dev[dev]) {
+        *p = reinterpret_cast<int32_t *>(g_noalloc_dev[dev]);
+        return cudaSuccess;
+    }
+    *p = nullptr;
+    return cudaSuccess;
+}

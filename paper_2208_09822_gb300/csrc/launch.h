@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "../../include/iaat.h"
 
 namespace iaat {
 cudaError_t prepare_fma(int dtype);
@@ -14,4 +15,13 @@ cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t s
 int tc_group_cap(int precision);        // largest stage footprint (bytes)
 constexpr int kTcPackRows = 128;        // rows of one MMA tile
 constexpr int kTcPackCols = 128;        // columns of one MMA tile
+// Allocation-free planning into caller-supplied arrays (host.cpp); used by
+// iaat_gemm_grouped_noalloc (kernels_fma.cu).
+iaat_status_t noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, int esz, int max_tasks, TaskDesc *tasks,
+                           uint32_t *bytes, double *cost, int32_t *order, TaskDesc *out, int32_t *gbeg,
+                           int64_t *ntasks_out, int64_t *ngroups_out);
+iaat_status_t noalloc_fail(iaat_status_t st, const char *msg);
+iaat_status_t noalloc_prepare(int dev);
+int noalloc_sm_count(int dev);
+cudaError_t noalloc_err_ptr(int32_t **p);   // NULL until the entry point's first call on the device
 }  // namespace iaat

@@ -68,6 +68,8 @@ def lib():
         L.iaat_plan_create.restype = S
         L.iaat_plan_create.argtypes = [P, ctypes.c_int64, I, I, ctypes.POINTER(PlanOptions),
                                        ctypes.POINTER(ctypes.c_void_p)]
+        L.iaat_gemm_grouped_noalloc.restype = S
+        L.iaat_gemm_grouped_noalloc.argtypes = [P, ctypes.c_int64, I, P]
         L.iaat_gemm_grouped.restype = S
         L.iaat_gemm_grouped.argtypes = [P, P]
         L.iaat_plan_check.restype = S
@@ -149,6 +151,14 @@ def iaat_plan_create(descs, dtype, precision=IAAT_PREC_DEFAULT, *, max_group_tas
     _check(lib().iaat_plan_create(descs.ctypes.data if len(descs) else None, len(descs), dtype, precision,
                                   ctypes.byref(opts), ctypes.byref(h)))
     return Plan(h.value)
+
+
+def iaat_gemm_grouped_noalloc(descs, dtype, stream=None):
+    """Allocation-free grouped GEMM (see include/iaat.h): descs is a
+    DESC_DTYPE array with device pointers inside."""
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    _check(lib().iaat_gemm_grouped_noalloc(descs.ctypes.data if len(descs) else None, len(descs), dtype,
+                                           _stream(stream)))
 
 
 def iaat_gemm_grouped(plan, stream=None):
