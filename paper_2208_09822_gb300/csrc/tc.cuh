@@ -2,23 +2,30 @@
 // and out: 3xBF16 split products, TF32, or FP16 inputs, FP32 accumulation in
 // tensor memory.
 //
-// The producer warp and the staging ring are those of the CUDA-core kernel.
-// The eight consumer warps take a stage's tasks pack by pack: a pack is a set
-// of tasks stacked into one 128-row MMA tile (task t owns rows R_t.., and the
-// columns C_t.. of the concatenated B), so several small instances share one
-// tensor-core pass and only the diagonal blocks of the product are kept.
-// Per pack:
-//   1. convert op(A) rows and op(B) columns of every task from the staged
-//      FP32 data into the canonical K-major (no swizzle) operand layout,
-//      splitting X = Xh + Xl for 3xBF16 (zero past each task's K);
-//   2. one thread issues the MMAs (K/16 or K/8 steps; three products per
-//      step for 3xBF16) into one of two TMEM accumulators and commits them to
-//      an mbarrier;
-//   3. while those run, the warps write the previous pack's results:
-//      tcgen05.ld of the accumulator rows, alpha*acc + beta*C0, stores of
-//      exactly the task's elements.
-// Every wait is bounded; a time-out sets the error word and the kernel frees
-// its tensor memory and returns.
+// Packs: the planner stacks the tasks of a stage into packs of at most 128
+// rows and 128 columns; task t owns rows R_t.. of the MMA tile and columns
+// C_t.. of the concatenated B, so several small instances share one
+// tensor-core pass and only the diagonal blocks of the product are kept
+// (the pack index, R_t and C_t travel in the task's variant/nbm/nbn fields).
+//
+// Warp roles (10 warps):
+//   0-3  converters: per 32-wide K-chunk of a pack, convert op(A) rows and
+//        op(B) columns of every task from the staged FP32 data into the
+//        canonical K-major (no swizzle) operand layout of one of two operand
+//        stages -- X = Xh + Xl (BF16) for 3xBF16, RN-rounded TF32, or FP16 --
+//        with zeros past each task's K;
+//   4-7  epilogue: when a pack's accumulator is complete, read each row of
+//        it from tensor memory (warp q owns lanes 32q..32q+31) and write
+//        alpha*acc + beta*C0 to exactly the task's elements;
+//   8    producer: streams stages into the shared-memory ring (shared with
+//        the CUDA-core kernel);
+//   9    MMA: one lane issues the chunk's MMAs into one of two accumulators
+//        and commits them to mbarriers that free the operand stage and, after
+//        a pack's last chunk, hand the accumulator to the epilogue.
+// Conversion of chunk c+1, the MMAs of chunk c and the epilogue of the
+// previous pack run at the same time.  Every wait is bounded; a time-out sets
+// the error word, every role leaves its loop, and the CTA frees its tensor
+// memory before returning.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -28,12 +35,14 @@
 namespace iaat {
 
 constexpr int kTc3xBF16 = 1, kTcTF32 = 2, kTcFP16 = 3;
-constexpr int kTcRows = 128;          // MMA M (TMEM lanes)
-constexpr int kTcMaxCols = 128;       // columns of one pack (MMA N <= 128)
-constexpr int kTcMaxK = 80;           // largest K of a task
-constexpr int kTcConsumerWarps = 8;
-constexpr int kTcThreads = 32 * (kTcConsumerWarps + 1);
-constexpr int kTcTmemCols = 256;      // two accumulators of 128 columns
+constexpr int kTcRows = 128;           // MMA M (TMEM lanes)
+constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
+constexpr int kTcKC = 32;              // K per operand stage
+constexpr int kTcStages = 2;           // operand stages
+constexpr int kTcConvWarps = 4, kTcEpiWarps = 4;
+constexpr int kTcWarpProducer = 8, kTcWarpMma = 9;
+constexpr int kTcThreads = 320;
+constexpr int kTcTmemCols = 256;       // two accumulators of 128 columns
 
 template <int P> struct TcTraits;
 template <> struct TcTraits<kTc3xBF16> {
@@ -48,27 +57,42 @@ template <> struct TcTraits<kTcFP16> {
 
 // Canonical K-major layout, no swizzle: core matrices of 8 rows x 16 bytes,
 // stored as 128 contiguous bytes; core matrices adjacent along K are 128 B
-// apart (leading byte offset), 8-row groups are kTcSBO<P> apart (stride byte
-// offset).  One operand buffer holds 128 rows x kTcMaxK.
-template <int P> IAAT_CE int tc_sbo() { return (kTcMaxK * TcTraits<P>::kOpBytes / 16) * 128; }
+// apart (leading byte offset), 8-row groups are tc_sbo() apart (stride byte
+// offset).  One operand buffer holds 128 rows x kTcKC.
+template <int P> IAAT_CE int tc_vpr() { return 16 / TcTraits<P>::kOpBytes; }          // values per core row
+template <int P> IAAT_CE int tc_kgroups() { return kTcKC / tc_vpr<P>(); }             // core matrices along K
+template <int P> IAAT_CE int tc_sbo() { return tc_kgroups<P>() * 128; }
 template <int P> IAAT_CE int tc_operand_bytes() { return (kTcRows / 8) * tc_sbo<P>(); }
-template <int P> IAAT_CE int tc_operands_total() { return 2 * TcTraits<P>::kTerms * tc_operand_bytes<P>(); }
+template <int P> IAAT_CE int tc_stage_bytes() { return 2 * TcTraits<P>::kTerms * tc_operand_bytes<P>(); }
 
-// shared-memory map (bytes)
-constexpr int kTcMmaBar = 192;        // two mbarriers
-constexpr int kTcTmemSlot = 208;      // tcgen05.alloc result
-constexpr int kTcFlag = 212;          // consumer-wide status word
-constexpr int kTcOperands = (kSmemCanon + 1023) & ~1023;
-template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + tc_operands_total<P>(); }
+// shared-memory map (bytes): the ring's barriers and stage records as in the
+// CUDA-core kernel, then this kernel's own barriers, then the operand stages
+constexpr int kTcExtra = kSmemSlots + kNumSlots * kSlotBytes;
+constexpr int kTcBarOpFull = kTcExtra;          // [2], 4 converter-warp arrivals
+constexpr int kTcBarOpEmpty = kTcExtra + 16;    // [2], tcgen05.commit
+constexpr int kTcBarAccFull = kTcExtra + 32;    // [2], tcgen05.commit
+constexpr int kTcBarAccEmpty = kTcExtra + 48;   // [2], 4 epilogue-warp arrivals
+constexpr int kTcTmemSlot = kTcExtra + 64;      // tcgen05.alloc result
+constexpr int kTcChunkInfo = kTcExtra + 80;     // [2] x 16 B
+constexpr int kTcOperands = (kTcExtra + 128 + 1023) & ~1023;
+static_assert(kTcExtra % 16 == 0, "barrier alignment");
+template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + kTcStages * tc_stage_bytes<P>(); }
 template <int P> IAAT_CE int tc_ring_bytes() { return (kSmemTotal - tc_ring_offset<P>()) & ~127; }
 template <int P> IAAT_CE int tc_max_group_bytes() { return tc_ring_bytes<P>() / 2; }
+
+struct ChunkInfo {      // converters -> MMA warp, one per operand stage
+    int32_t nt;         // MMA N of the pack
+    int32_t kc;         // K of this chunk (multiple of the MMA K step; 0: no product)
+    int32_t flags;      // bit 0 first chunk of the pack, bit 1 last, bit 2 end of work
+    int32_t pad;
+};
+constexpr int kChunkFirst = 1, kChunkLast = 2, kChunkEnd = 4;
 
 // ------------------------------------------------------------ tcgen05 PTX
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kTcConsumerWarps * 32) : "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols)
 {
@@ -162,7 +186,7 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Convert the 16-byte core-matrix row of VPR FP32 values x[] and store it
+// Convert one 16-byte core-matrix row (tc_vpr<P>() FP32 values) and store it
 // (hi, and lo for 3xBF16) at byte offset `off` of the term buffers.
 template <int P>
 __device__ __forceinline__ void store_row(char *t0, char *t1, uint32_t off, const float *x)
@@ -189,278 +213,384 @@ __device__ __forceinline__ void store_row(char *t0, char *t1, uint32_t off, cons
     }
 }
 
-// Convert rows [0, rows) of one operand of a task into canonical rows
-// [row0, row0 + rows) of the term buffers, K-groups [0, ngroups).
-// raw(i, k) = src + i*si + k*sk (bytes); values with k >= K are zero.
-// kfast: lanes run along the K-groups (raw contiguous in k), else along rows.
+// Convert one task operand's K-chunk [k0, k0 + kc) into canonical rows
+// [row0, row0 + rows) of an operand stage.  raw(i, k) = src + i*si + k*sk.
+// Values with k >= K are zero.  kcontig: the staged data is contiguous along
+// k, so a lane takes one core-matrix row (lanes: rows x K-groups); otherwise
+// it is contiguous along the rows and lanes run along the rows.
 template <int P>
-__device__ __forceinline__ void convert_operand(char *t0, char *t1, const char *src, int si, int sk, int rows,
-                                                int K, int row0, int ngroups, bool kfast)
+__device__ __forceinline__ void convert_chunk(char *t0, char *t1, const char *src, int si, int sk, int rows, int K,
+                                              int row0, int k0, int kc, bool kcontig)
 {
-    constexpr int VPR = 16 / TcTraits<P>::kOpBytes;   // values per core-matrix row
+    constexpr int VPR = tc_vpr<P>();
+    constexpr int KGM = tc_kgroups<P>();
     constexpr int SBO = tc_sbo<P>();
     const int lane = (int)lane_id();
-    if (rows <= 0 || ngroups <= 0)
-        return;
-    int lg_fast;   // log2 of lanes along the fast dimension
-    const int fast_len = kfast ? ngroups : rows;
-    lg_fast = fast_len >= 32 ? 5 : (32 - __clz(fast_len - 1));   // ceil(log2)
-    if (fast_len <= 1)
-        lg_fast = 0;
-    const int nfast = 1 << lg_fast;
-    const int lf = lane & (nfast - 1);
-    const int ls = lane >> lg_fast;
-    const int sstep = 32 >> lg_fast;
-    const int slow_len = kfast ? rows : ngroups;
+    const int ng = kc / VPR;
+    if (kcontig) {
+        constexpr int RPS = 32 / KGM;            // rows per warp step
+        const int g = lane % KGM, rr = lane / KGM;
+        if (g < ng) {
+            const int kb = k0 + g * VPR;
 #pragma unroll 1
-    for (int s0 = 0; s0 < slow_len; s0 += sstep) {
-        const int s = s0 + ls;
-#pragma unroll 1
-        for (int f = lf; f < fast_len && s < slow_len; f += nfast) {
-            const int i = kfast ? s : f;
-            const int g = kfast ? f : s;
-            const int k0 = g * VPR;
-            float x[8];
-            const char *p = src + i * si + k0 * sk;
+            for (int r = rr; r < rows; r += RPS) {
+                const char *p = src + r * si + kb * sk;
+                float x[8];
 #pragma unroll
-            for (int e = 0; e < VPR; ++e)
-                x[e] = (k0 + e < K) ? *reinterpret_cast<const float *>(p + e * sk) : 0.0f;
-            const int r = row0 + i;
-            const uint32_t off = (uint32_t)((r >> 3) * SBO + g * 128 + (r & 7) * 16);
-            store_row<P>(t0, t1, off, x);
+                for (int e = 0; e < VPR; ++e)
+                    x[e] = (kb + e < K) ? *reinterpret_cast<const float *>(p + e * sk) : 0.0f;
+                const int row = row0 + r;
+                store_row<P>(t0, t1, (uint32_t)((row >> 3) * SBO + g * 128 + (row & 7) * 16), x);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int r = lane; r < rows; r += 32) {
+            const int row = row0 + r;
+            const char *p = src + r * si;
+#pragma unroll 1
+            for (int g = 0; g < ng; ++g) {
+                const int kb = k0 + g * VPR;
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < VPR; ++e)
+                    x[e] = (kb + e < K) ? *reinterpret_cast<const float *>(p + (kb + e) * sk) : 0.0f;
+                store_row<P>(t0, t1, (uint32_t)((row >> 3) * SBO + g * 128 + (row & 7) * 16), x);
+            }
         }
     }
 }
 
-template <int P>
-__device__ void tc_epilogue(const SmemMap &S, const TaskRec *recs, unsigned mask, bool zero_acc, int NT, int cw,
-                            uint32_t dtmem);
-
-struct PackTask {   // fields of one task as the consumer warps need them
-    int M, N, K, R, Cc, ta, tb, offA, offB, csA, csB;
+struct TcSmem {
+    SmemMap S;
+    __device__ uint32_t op_full(int b) const { return S.sbase + kTcBarOpFull + 8 * b; }
+    __device__ uint32_t op_empty(int b) const { return S.sbase + kTcBarOpEmpty + 8 * b; }
+    __device__ uint32_t acc_full(int a) const { return S.sbase + kTcBarAccFull + 8 * a; }
+    __device__ uint32_t acc_empty(int a) const { return S.sbase + kTcBarAccEmpty + 8 * a; }
+    __device__ ChunkInfo *info(int b) const { return reinterpret_cast<ChunkInfo *>(S.base + kTcChunkInfo) + b; }
 };
 
-template <int P>
-__device__ void tc_consumer(const KParams &KP, const SmemMap &S, int cw, uint32_t tmem)
-{
-    const Params &P_ = KP.p;
-    const int lane = (int)lane_id();
-    constexpr int KS = TcTraits<P>::kKStep;
-    constexpr int VPR = 16 / TcTraits<P>::kOpBytes;
-    constexpr int OPB = tc_operand_bytes<P>();
-    char *const opbase = S.base + kTcOperands;
-    char *const A0 = opbase;
-    char *const A1 = opbase + OPB;                                   // 3xBF16: lo
-    char *const B0 = opbase + TcTraits<P>::kTerms * OPB;
-    char *const B1 = B0 + OPB;
-    volatile int32_t *flag = reinterpret_cast<volatile int32_t *>(S.base + kTcFlag);
-    const uint32_t mbar0 = S.sbase + kTcMmaBar;
-    uint32_t mma_phase[2] = {0u, 0u};
-    int buf = 0;
-    bool alive = true;
+// Per-warp view of a stage's tasks: lane t holds task t's fields.
+struct LaneTask {
+    int M, N, K, R, Cc, pack, ta, tb, offA, offB, csA, csB;
+};
 
+__device__ __forceinline__ LaneTask load_lane_task(const TaskRec *recs, int nt)
+{
+    const int lane = (int)lane_id();
+    LaneTask me{0, 0, 0, 0, 0, 1 << 20, 0, 0, 0, 0, 0, 0};
+    if (lane < nt) {
+        const TaskRec &r = recs[lane];
+        me = LaneTask{r.M, r.N, r.K, r.nbm, r.nbn, r.variant, r.ta, r.tb, r.offA, r.offB, r.csA, r.csB};
+    }
+    return me;
+}
+
+__device__ __forceinline__ int warp_max(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Pack p's task mask, K (rounded to the MMA K step) and MMA N.
+template <int P>
+__device__ __forceinline__ void pack_shape(const LaneTask &me, int nt, int p, unsigned &mask, int &KT, int &NT)
+{
+    constexpr int KS = TcTraits<P>::kKStep;
+    const int lane = (int)lane_id();
+    const bool in = lane < nt && me.pack == p;
+    mask = __ballot_sync(0xffffffffu, in);
+    const int kmax = warp_max(in ? me.K : 0);
+    const int cmax = warp_max(in ? me.Cc + me.N : 0);
+    KT = (kmax + KS - 1) / KS * KS;
+    NT = max(16, (cmax + 15) & ~15);
+}
+
+// Bounded wait on an mbarrier phase by every lane of a warp.  Each lane
+// performs the acquire itself, so each lane's later reads of what was
+// published with the barrier (stage records, chunk records, operand data)
+// see the new values; lanes that only learned of the phase from another lane
+// could read stale records, take different branches and deadlock the warp at
+// its next collective.  The outcome is made warp-uniform.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+{
+    const bool ok = mbar_wait(bar, parity, kWaitLimitNs);
+    return __all_sync(0xffffffffu, ok);
+}
+
+template <int P>
+__device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
+{
+    const Params &Pm = KP.p;
+    const int lane = (int)lane_id();
+    constexpr int OPB = tc_operand_bytes<P>();
+    int b = 0;
+    uint32_t bpar = 0;     // parity of the operand stages' current round
+    int uses = 0;          // chunks handed to the MMA warp so far
+    bool alive = true;
     for (int i = 0; alive; ++i) {
         const int g = sched_group(i, blockIdx.x, gridDim.x);
-        if (g >= P_.ngroups)
+        if (g >= Pm.ngroups)
             break;
         const int slot = i % kNumSlots;
-        if (cw == 0) {
-            int ok = 1;
+        if (!warp_wait(T.S.full(slot), (uint32_t)((i / kNumSlots) & 1))) {
             if (lane == 0)
-                ok = mbar_wait(S.full(slot), (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (lane == 0) {
-                *flag = ok;
-                if (!ok)
-                    set_error(P_.err, kErrTimeoutFull);
-            }
-        }
-        consumer_bar();
-        if (!*flag) {
+                set_error(Pm.err, kErrTimeoutFull);
             alive = false;
             break;
         }
-        const SlotHeader *hd = S.header(slot);
-        const TaskRec *recs = S.recs(slot);
-        const int nt = hd->ntasks;
-        // lane t keeps task t's fields
-        PackTask me{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        int pack = 1 << 20;
-        if (lane < nt) {
-            const TaskRec &r = recs[lane];
-            me = PackTask{r.M, r.N, r.K, r.nbm, r.nbn, r.ta, r.tb, r.offA, r.offB, r.csA, r.csB};
-            pack = r.variant;
-        }
-        int npacks = lane < nt ? pack + 1 : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            npacks = max(npacks, __shfl_xor_sync(0xffffffffu, npacks, o));
-
-        unsigned prev_mask = 0;
-        int prev_nt = 0;
-        bool prev_zero = false;
+        const TaskRec *recs = T.S.recs(slot);
+        const int nt = T.S.header(slot)->ntasks;
+        const LaneTask me = load_lane_task(recs, nt);
+        const int npacks = warp_max(lane < nt ? me.pack + 1 : 0);
         for (int p = 0; p < npacks && alive; ++p) {
-            const unsigned mask = __ballot_sync(0xffffffffu, lane < nt && pack == p);
-            int kmax = (mask >> lane) & 1 ? me.K : 0;
-            int cmax = (mask >> lane) & 1 ? me.Cc + me.N : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-                cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-            }
-            const int KT = (kmax + KS - 1) / KS * KS;
-            const int NT = max(16, (cmax + 15) & ~15);
-            const int ngroups = KT / VPR;
-            // 1. conversion: the pack's tasks dealt round-robin to the warps
-            if (KT > 0) {
-                int q = 0;
-                for (unsigned m = mask; m; m &= m - 1, ++q) {
-                    const int t = __ffs(m) - 1;
-                    if ((q % kTcConsumerWarps) != cw)
-                        continue;
-                    PackTask tk;
-                    tk.M = __shfl_sync(0xffffffffu, me.M, t);
-                    tk.N = __shfl_sync(0xffffffffu, me.N, t);
-                    tk.K = __shfl_sync(0xffffffffu, me.K, t);
-                    tk.R = __shfl_sync(0xffffffffu, me.R, t);
-                    tk.Cc = __shfl_sync(0xffffffffu, me.Cc, t);
-                    tk.ta = __shfl_sync(0xffffffffu, me.ta, t);
-                    tk.tb = __shfl_sync(0xffffffffu, me.tb, t);
-                    tk.offA = __shfl_sync(0xffffffffu, me.offA, t);
-                    tk.offB = __shfl_sync(0xffffffffu, me.offB, t);
-                    tk.csA = __shfl_sync(0xffffffffu, me.csA, t);
-                    tk.csB = __shfl_sync(0xffffffffu, me.csB, t);
-                    // op(A)(i, k): stored A[i + k*lda] (N) or A[k + i*lda] (T)
-                    const int ai = tk.ta ? tk.csA : 4, ak = tk.ta ? 4 : tk.csA;
-                    convert_operand<P>(A0, A1, S.base + tk.offA, ai, ak, tk.M, tk.K, tk.R, ngroups, tk.ta != 0);
-                    // op(B)(k, n) as an N x K operand: stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
-                    const int bi = tk.tb ? 4 : tk.csB, bk = tk.tb ? tk.csB : 4;
-                    convert_operand<P>(B0, B1, S.base + tk.offB, bi, bk, tk.N, tk.K, tk.Cc, ngroups, tk.tb == 0);
+            unsigned mask;
+            int KT, NT;
+            pack_shape<P>(me, nt, p, mask, KT, NT);
+            const int nch = KT > 0 ? (KT + kTcKC - 1) / kTcKC : 1;
+            for (int c = 0; c < nch; ++c) {
+                // the MMAs that read this stage one round ago must be done
+                if (uses >= kTcStages && !warp_wait(T.op_empty(b), bpar ^ 1u)) {
+                    if (lane == 0)
+                        set_error(Pm.err, kErrTimeoutEmpty);
+                    alive = false;
+                    break;
+                }
+                const int k0 = c * kTcKC;
+                const int kc = KT > 0 ? min(kTcKC, KT - k0) : 0;
+                char *base = T.S.base + kTcOperands + b * tc_stage_bytes<P>();
+                char *A0 = base, *A1 = base + OPB;
+                char *B0 = base + TcTraits<P>::kTerms * OPB, *B1 = B0 + OPB;
+                if (kc > 0) {
+                    // (task, operand) items dealt round-robin to the converter warps
+                    int q = 0;
+                    for (unsigned m = mask; m; m &= m - 1) {
+                        const int t = __ffs(m) - 1;
+                        for (int op = 0; op < 2; ++op, ++q) {
+                            if ((q & (kTcConvWarps - 1)) != cw)
+                                continue;
+                            const int K = __shfl_sync(0xffffffffu, me.K, t);
+                            if (op == 0) {
+                                const int M = __shfl_sync(0xffffffffu, me.M, t);
+                                const int ta = __shfl_sync(0xffffffffu, me.ta, t);
+                                const int offA = __shfl_sync(0xffffffffu, me.offA, t);
+                                const int csA = __shfl_sync(0xffffffffu, me.csA, t);
+                                const int R = __shfl_sync(0xffffffffu, me.R, t);
+                                // op(A)(i, k): stored A[i + k*lda] (N) or A[k + i*lda] (T)
+                                convert_chunk<P>(A0, A1, T.S.base + offA, ta ? csA : 4, ta ? 4 : csA, M, K, R, k0, kc,
+                                                 ta != 0);
+                            } else {
+                                const int N = __shfl_sync(0xffffffffu, me.N, t);
+                                const int tb = __shfl_sync(0xffffffffu, me.tb, t);
+                                const int offB = __shfl_sync(0xffffffffu, me.offB, t);
+                                const int csB = __shfl_sync(0xffffffffu, me.csB, t);
+                                const int Cc = __shfl_sync(0xffffffffu, me.Cc, t);
+                                // B operand row n = column n of op(B): stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
+                                convert_chunk<P>(B0, B1, T.S.base + offB, tb ? 4 : csB, tb ? csB : 4, N, K, Cc, k0, kc,
+                                                 tb == 0);
+                            }
+                        }
+                    }
+                }
+                if (cw == 0 && lane == 0) {
+                    ChunkInfo *ci = T.info(b);
+                    ci->nt = NT;
+                    ci->kc = kc;
+                    ci->flags = (c == 0 ? kChunkFirst : 0) | (c == nch - 1 ? kChunkLast : 0);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(T.op_full(b));
+                ++uses;
+                if (++b == kTcStages) {
+                    b = 0;
+                    bpar ^= 1u;
                 }
             }
-            fence_proxy_async();
-            tc_fence_before();
-            consumer_bar();
-            // 2. MMAs of this pack into accumulator `buf`
-            if (cw == 0 && lane == 0 && KT > 0) {
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * kTcMaxCols);
-                const uint32_t idesc = tc_idesc<P>(NT);
-                const uint32_t a0 = smem_addr(A0), a1 = smem_addr(A1), b0 = smem_addr(B0), b1 = smem_addr(B1);
-                constexpr uint32_t SBO = (uint32_t)tc_sbo<P>();
-                for (int ks = 0; ks < KT / KS; ++ks) {
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(T.S.empty(slot));
+    }
+    // end-of-work marker for the MMA warp
+    if (alive && (uses < kTcStages || warp_wait(T.op_empty(b), bpar ^ 1u))) {
+        if (cw == 0 && lane == 0) {
+            ChunkInfo *ci = T.info(b);
+            ci->nt = 16;
+            ci->kc = 0;
+            ci->flags = kChunkEnd;
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(T.op_full(b));
+    }
+}
+
+template <int P>
+__device__ void tc_mma_warp(const KParams &KP, const TcSmem &T, uint32_t tmem)
+{
+    const Params &Pm = KP.p;
+    const int lane = (int)lane_id();
+    constexpr int KS = TcTraits<P>::kKStep;
+    constexpr int OPB = tc_operand_bytes<P>();
+    constexpr uint32_t SBO = (uint32_t)tc_sbo<P>();
+    int b = 0, a = 0;
+    uint32_t bpar = 0;
+    uint32_t apar[2] = {0u, 0u};
+    int acc_uses[2] = {0, 0};
+    int commits[kTcStages] = {0, 0};   // tcgen05.commit arrivals sent to op_empty[b]
+    for (;;) {
+        if (!warp_wait(T.op_full(b), bpar)) {
+            if (lane == 0)
+                set_error(Pm.err, kErrTimeoutFull);
+            break;
+        }
+        const ChunkInfo ci = *T.info(b);
+        if (ci.flags & kChunkEnd)
+            break;
+        if ((ci.flags & kChunkFirst) && acc_uses[a] > 0) {
+            // the epilogue must have drained this accumulator
+            if (!warp_wait(T.acc_empty(a), apar[a] ^ 1u)) {
+                if (lane == 0)
+                    set_error(Pm.err, kErrTimeoutEmpty);
+                break;
+            }
+        }
+        if (lane == 0) {
+            tc_fence_after();
+            if (ci.kc > 0) {
+                const uint32_t d = tmem + (uint32_t)(a * kTcMaxCols);
+                const uint32_t idesc = tc_idesc<P>(ci.nt);
+                const uint32_t base = smem_addr(T.S.base + kTcOperands + b * tc_stage_bytes<P>());
+                const uint32_t a0 = base, a1 = base + OPB;
+                const uint32_t b0 = base + TcTraits<P>::kTerms * OPB, b1 = b0 + OPB;
+                const bool first = (ci.flags & kChunkFirst) != 0;
+                for (int ks = 0; ks < ci.kc / KS; ++ks) {
                     const uint32_t o = (uint32_t)ks * 256u;   // two core matrices along K
+                    const uint32_t accum = (first && ks == 0) ? 0u : 1u;
                     if constexpr (P == kTc3xBF16) {
-                        tc_mma<P>(d, smem_desc(a1 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, ks > 0);
+                        tc_mma<P>(d, smem_desc(a1 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
                         tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b1 + o, 128, SBO), idesc, 1);
                         tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, 1);
                     } else {
-                        tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, ks > 0);
+                        tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
                     }
                 }
-                tc_commit(mbar0 + 8u * (uint32_t)buf);
             }
-            // 3. results of the previous pack while these MMAs run
-            if (p > 0)
-                tc_epilogue<P>(S, recs, prev_mask, prev_zero, prev_nt, cw, tmem + (uint32_t)((buf ^ 1) * kTcMaxCols));
-            // wait for this pack's MMAs: the operand buffers are free again
-            if (cw == 0) {
-                int ok = 1;
-                if (lane == 0 && KT > 0) {
-                    ok = mbar_wait(mbar0 + 8u * (uint32_t)buf, mma_phase[buf], kWaitLimitNs) ? 1 : 0;
-                    if (!ok)
-                        set_error(P_.err, kErrTimeoutFull);
-                }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (lane == 0)
-                    *flag = ok;
-            }
-            if (KT > 0)
-                mma_phase[buf] ^= 1u;
-            tc_fence_before();
-            consumer_bar();
-            tc_fence_after();
-            if (!*flag) {
-                alive = false;
-                break;
-            }
-            prev_mask = mask;
-            prev_zero = KT == 0;   // no product: the accumulator is not read
-            prev_nt = NT;
-            buf ^= 1;
+            tc_commit(T.op_empty(b));
+            if (ci.flags & kChunkLast)
+                tc_commit(T.acc_full(a));
         }
-        if (!alive)
-            break;
-        if (npacks > 0)
-            tc_epilogue<P>(S, recs, prev_mask, prev_zero, prev_nt, cw, tmem + (uint32_t)((buf ^ 1) * kTcMaxCols));
-        tc_fence_before();
-        consumer_bar();
-        if (cw == 0 && lane == 0)
-            mbar_arrive(S.empty(slot));
+        __syncwarp();
+        ++commits[b];
+        if (ci.flags & kChunkLast) {
+            ++acc_uses[a];
+            apar[a] ^= 1u;
+            a ^= 1;
+        }
+        if (++b == kTcStages) {
+            b = 0;
+            bpar ^= 1u;
+        }
     }
-    // leave: every consumer warp reaches this barrier on both paths
-    tc_fence_before();
-    consumer_bar();
-    tc_fence_after();
-    if (cw == 0)
-        tmem_dealloc(tmem, kTcTmemCols);
+    // No asynchronous arrival may reach this CTA's shared memory after it
+    // exits: wait (bounded) for the last commit to each operand-stage barrier,
+    // which no other role waits for.  (The accumulator commits are all
+    // waited for by the epilogue.)
+    if (lane == 0) {
+        for (int bb = 0; bb < kTcStages; ++bb)
+            if (commits[bb] > 0 &&
+                !mbar_wait(T.op_empty(bb), (uint32_t)((commits[bb] - 1) & 1), kWaitLimitNs))
+                set_error(Pm.err, kErrTimeoutFull);
+    }
+    __syncwarp();
 }
 
-// Results of one pack: thread (warp cw, lane) owns accumulator row
-// 32*(cw%4) + lane; warps cw < 4 take the even 16-column chunks, the others
-// the odd ones.  `mask` bit t: task t is in the pack; zero_acc: the pack
-// had no product (K = 0 or alpha = 0 everywhere), acc = 0.
 template <int P>
-__device__ void tc_epilogue(const SmemMap &S, const TaskRec *recs, unsigned mask, bool zero_acc, int NT, int cw,
-                            uint32_t dtmem)
+__device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, uint32_t tmem)
 {
+    const Params &Pm = KP.p;
     const int lane = (int)lane_id();
-    const int row = 32 * (cw & 3) + lane;
-    // find this row's task
-    int t = -1;
-    for (unsigned m = mask; m; m &= m - 1) {
-        const int c = __ffs(m) - 1;
-        const int R = recs[c].nbm, M = recs[c].M;
-        if (row >= R && row < R + M)
-            t = c;
-    }
-    int Cc = 0, N = 0, i = 0, ldc = 0, csC = 0, offC = 0;
-    float alpha = 0.f, beta = 0.f;
-    bool readc = false;
-    float *C = nullptr;
-    if (t >= 0) {
-        const TaskRec &r = recs[t];
-        Cc = r.nbn; N = r.N; i = row - r.nbm; ldc = r.ldc; csC = r.csC; offC = r.offC;
-        alpha = (float)r.alpha; beta = (float)r.beta;
-        readc = (r.flags & kFlagReadC) != 0;
-        C = reinterpret_cast<float *>(r.C);
-    }
-    const uint32_t taddr = dtmem + ((uint32_t)(32 * (cw & 3)) << 16);
-    for (int ch = (cw >> 2); ch * 16 < NT; ch += 2) {
-        const int j0 = ch * 16;
-        const bool need = t >= 0 && Cc < j0 + 16 && j0 < Cc + N;
-        if (!__any_sync(0xffffffffu, need))
-            continue;
-        float v[16];
-        if (zero_acc) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                v[u] = 0.f;
-        } else {
-            tmem_ld16(taddr + (uint32_t)j0, v);
+    const int row = 32 * ew + lane;                 // accumulator row (TMEM lane) of this thread
+    const uint32_t lane_base = (uint32_t)(32 * ew) << 16;
+    int a = 0;
+    uint32_t apar[2] = {0u, 0u};
+    for (int i = 0;; ++i) {
+        const int g = sched_group(i, blockIdx.x, gridDim.x);
+        if (g >= Pm.ngroups)
+            break;
+        const int slot = i % kNumSlots;
+        if (!warp_wait(T.S.full(slot), (uint32_t)((i / kNumSlots) & 1))) {
+            if (lane == 0)
+                set_error(Pm.err, kErrTimeoutFull);
+            return;
         }
-        if (need) {
+        const TaskRec *recs = T.S.recs(slot);
+        const int nt = T.S.header(slot)->ntasks;
+        const LaneTask me = load_lane_task(recs, nt);
+        const int npacks = warp_max(lane < nt ? me.pack + 1 : 0);
+        for (int p = 0; p < npacks; ++p) {
+            unsigned mask;
+            int KT, NT;
+            pack_shape<P>(me, nt, p, mask, KT, NT);
+            if (!warp_wait(T.acc_full(a), apar[a])) {
+                if (lane == 0)
+                    set_error(Pm.err, kErrTimeoutFull);
+                return;
+            }
+            apar[a] ^= 1u;
+            tc_fence_after();
+            const uint32_t dt = tmem + (uint32_t)(a * kTcMaxCols) + lane_base;
+            // tasks whose rows meet this warp's 32 rows
+            const unsigned rows_mask = __ballot_sync(
+                0xffffffffu, ((mask >> lane) & 1) && me.R < 32 * ew + 32 && me.R + me.M > 32 * ew);
+            for (unsigned m = rows_mask; m; m &= m - 1) {
+                const int t = __ffs(m) - 1;
+                const TaskRec &r = recs[t];
+                const int R = r.nbm, M = r.M, Cc = r.nbn, N = r.N;
+                const bool mine = row >= R && row < R + M;
+                const int i_ = mine ? row - R : 0;
+                const float alpha = (float)r.alpha, beta = (float)r.beta;
+                const bool readc = (r.flags & kFlagReadC) != 0;
+                float *C = reinterpret_cast<float *>(r.C) + i_;
+                const int64_t ldc = r.ldc;
+                const char *c0 = T.S.base + r.offC + i_ * 4;
+                const int csC = r.csC;
+                for (int j0 = Cc & ~15; j0 < Cc + N; j0 += 16) {
+                    float v[16];
+                    if (KT > 0) {
+                        tmem_ld16(dt + (uint32_t)j0, v);
+                    } else {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int j = j0 + u - Cc;
-                if (j >= 0 && j < N) {
-                    float c = alpha * v[u];
-                    if (readc)
-                        c = fmaf(beta, *reinterpret_cast<const float *>(S.base + offC + j * csC + i * 4), c);
-                    C[i + (int64_t)j * ldc] = c;
+                        for (int u = 0; u < 16; ++u)
+                            v[u] = 0.f;
+                    }
+                    if (mine) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int j = j0 + u - Cc;
+                            if (j >= 0 && j < N) {
+                                float c = alpha * v[u];
+                                if (readc)
+                                    c = fmaf(beta, *reinterpret_cast<const float *>(c0 + j * csC), c);
+                                C[j * ldc] = c;
+                            }
+                        }
+                    }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(T.acc_empty(a));
+            a ^= 1;
         }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(T.S.empty(slot));
     }
 }
 
@@ -468,32 +598,44 @@ template <int P>
 __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_constant__ KParams KP)
 {
     extern __shared__ __align__(1024) char smem_tc[];
-    char *smem = smem_tc;
-    SmemMap S;
-    S.base = smem;
-    S.sbase = smem_addr(smem);
-    S.ring_off = (uint32_t)tc_ring_offset<P>();
-    S.ring_bytes = (uint32_t)tc_ring_bytes<P>();
+    TcSmem T;
+    T.S.base = smem_tc;
+    T.S.sbase = smem_addr(smem_tc);
+    T.S.ring_off = (uint32_t)tc_ring_offset<P>();
+    T.S.ring_bytes = (uint32_t)tc_ring_bytes<P>();
     const int warp = threadIdx.x / 32;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNumSlots; ++s) {
-            mbar_init(S.full(s), 1);
-            mbar_init(S.empty(s), 1);
+            mbar_init(T.S.full(s), 1);
+            mbar_init(T.S.empty(s), kTcConvWarps + kTcEpiWarps);
         }
-        mbar_init(S.sbase + kTcMmaBar, 1);
-        mbar_init(S.sbase + kTcMmaBar + 8, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(T.op_full(b), kTcConvWarps);
+            mbar_init(T.op_empty(b), 1);
+            mbar_init(T.acc_full(b), 1);
+            mbar_init(T.acc_empty(b), kTcEpiWarps);
+        }
         fence_barrier_init();
     }
     if (warp == 0)
-        tmem_alloc(S.sbase + kTcTmemSlot, kTcTmemCols);
+        tmem_alloc(T.S.sbase + kTcTmemSlot, kTcTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + kTcTmemSlot);
-    if (warp == kTcConsumerWarps)
-        producer_loop<4>(KP, S);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem_tc + kTcTmemSlot);
+    if (warp < kTcConvWarps)
+        tc_converters<P>(KP, T, warp);
+    else if (warp < kTcConvWarps + kTcEpiWarps)
+        tc_epilogue_warps<P>(KP, T, warp - kTcConvWarps, tmem);
+    else if (warp == kTcWarpProducer)
+        producer_loop<4>(KP, T.S);
     else
-        tc_consumer<P>(KP, S, warp, tmem);
+        tc_mma_warp<P>(KP, T, tmem);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        tmem_dealloc(tmem, kTcTmemCols);
 }
 
 }  // namespace iaat
