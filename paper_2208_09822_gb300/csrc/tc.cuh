@@ -8,18 +8,20 @@
 // tensor-core pass and only the diagonal blocks of the product are kept
 // (the pack index, R_t and C_t travel in the task's variant/nbm/nbn fields).
 //
-// Warp roles (10 warps):
-//   0-3  converters: per 32-wide K-chunk of a pack, convert op(A) rows and
-//        op(B) columns of every task from the staged FP32 data into the
-//        canonical K-major (no swizzle) operand layout of one of two operand
-//        stages -- X = Xh + Xl (BF16) for 3xBF16, RN-rounded TF32, or FP16 --
-//        with zeros past each task's K;
-//   4-7  epilogue: when a pack's accumulator is complete, read each row of
-//        it from tensor memory (warp q owns lanes 32q..32q+31) and write
-//        alpha*acc + beta*C0 to exactly the task's elements;
-//   8    producer: streams stages into the shared-memory ring (shared with
+// Warp roles (18 warps):
+//   0-7  converters: per 32-wide K-chunk of a pack, every thread converts one
+//        row of the 128-row tile -- warps 0-3 the rows of op(A), warps 4-7
+//        the rows of op(B)^T -- from the staged FP32 data into the canonical
+//        K-major (no swizzle) operand layout of one of two operand stages:
+//        X = Xh + Xl (BF16) for 3xBF16, RN-rounded TF32, or FP16, with zeros
+//        past the row's K;
+//   8-15 epilogue: when a pack's accumulator is complete, read each row of
+//        it from tensor memory (warps 8+q and 12+q own lanes 32q..32q+31 and
+//        take alternate 16-column chunks) and write alpha*acc + beta*C0 to
+//        exactly the task's elements;
+//   16   producer: streams stages into the shared-memory ring (shared with
 //        the CUDA-core kernel);
-//   9    MMA: one lane issues the chunk's MMAs into one of two accumulators
+//   17   MMA: one lane issues the chunk's MMAs into one of two accumulators
 //        and commits them to mbarriers that free the operand stage and, after
 //        a pack's last chunk, hand the accumulator to the epilogue.
 // Conversion of chunk c+1, the MMAs of chunk c and the epilogue of the
@@ -39,9 +41,9 @@ constexpr int kTcRows = 128;           // MMA M (TMEM lanes)
 constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
 constexpr int kTcKC = 32;              // K per operand stage
 constexpr int kTcStages = 2;           // operand stages
-constexpr int kTcConvWarps = 4, kTcEpiWarps = 4;
-constexpr int kTcWarpProducer = 8, kTcWarpMma = 9;
-constexpr int kTcThreads = 320;
+constexpr int kTcConvWarps = 8, kTcEpiWarps = 8;
+constexpr int kTcWarpProducer = 16, kTcWarpMma = 17;
+constexpr int kTcThreads = 576;
 constexpr int kTcTmemCols = 256;       // two accumulators of 128 columns
 
 template <int P> struct TcTraits;
@@ -316,8 +318,14 @@ __device__ __forceinline__ void pack_shape(const LaneTask &me, int nt, int p, un
 // its next collective.  The outcome is made warp-uniform.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
 {
-    const bool ok = mbar_wait(bar, parity, kWaitLimitNs);
-    return __all_sync(0xffffffffu, ok);
+    // lane 0 does the (suspending) wait; then every lane confirms the
+    // completed phase with its own try_wait, which is its acquire
+    int ok = 1;
+    if (lane_id() == 0)
+        ok = mbar_wait(bar, parity, kWaitLimitNs) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    const bool mine = ok && mbar_wait(bar, parity, kWaitLimitNs);
+    return __all_sync(0xffffffffu, mine);
 }
 
 template <int P>
@@ -326,6 +334,9 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
     const Params &Pm = KP.p;
     const int lane = (int)lane_id();
     constexpr int OPB = tc_operand_bytes<P>();
+    constexpr int VPR = tc_vpr<P>();
+    const int side = cw >> 2;                 // 0: A rows, 1: B rows
+    const int row = 32 * (cw & 3) + lane;     // this thread's pack row
     int b = 0;
     uint32_t bpar = 0;     // parity of the operand stages' current round
     int uses = 0;          // chunks handed to the MMA warp so far
@@ -350,6 +361,29 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
             int KT, NT;
             pack_shape<P>(me, nt, p, mask, KT, NT);
             const int nch = KT > 0 ? (KT + kTcKC - 1) / kTcKC : 1;
+            // the task owning this thread's row of the pack (A rows for warps
+            // 0-3, B rows for warps 4-7), and where that row's data sits
+            int my_task = -1;
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int c = __ffs(m) - 1;
+                const int lo = __shfl_sync(0xffffffffu, side == 0 ? me.R : me.Cc, c);
+                const int len = __shfl_sync(0xffffffffu, side == 0 ? me.M : me.N, c);
+                if (row >= lo && row < lo + len)
+                    my_task = c;
+            }
+            const int src_lane = my_task >= 0 ? my_task : 0;
+            const int t_lo = __shfl_sync(0xffffffffu, side == 0 ? me.R : me.Cc, src_lane);
+            const int my_K = __shfl_sync(0xffffffffu, me.K, src_lane);
+            const int t_tr = __shfl_sync(0xffffffffu, side == 0 ? me.ta : me.tb, src_lane);
+            const int t_off = __shfl_sync(0xffffffffu, side == 0 ? me.offA : me.offB, src_lane);
+            const int t_cs = __shfl_sync(0xffffffffu, side == 0 ? me.csA : me.csB, src_lane);
+            // A row i: stored A[i + k*lda] (N) or A[k + i*lda] (T);
+            // B row n (column n of op(B)): stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
+            const bool kcontig = side == 0 ? t_tr != 0 : t_tr == 0;
+            const int my_si = kcontig ? t_cs : 4;
+            const int my_sk = kcontig ? 4 : t_cs;
+            const char *my_src = T.S.base + t_off + (row - t_lo) * my_si;
+            const uint32_t row_off = (uint32_t)((row >> 3) * tc_sbo<P>() + (row & 7) * 16);
             for (int c = 0; c < nch; ++c) {
                 // the MMAs that read this stage one round ago must be done
                 if (uses >= kTcStages && !warp_wait(T.op_empty(b), bpar ^ 1u)) {
@@ -363,35 +397,26 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
                 char *base = T.S.base + kTcOperands + b * tc_stage_bytes<P>();
                 char *A0 = base, *A1 = base + OPB;
                 char *B0 = base + TcTraits<P>::kTerms * OPB, *B1 = B0 + OPB;
-                if (kc > 0) {
-                    // (task, operand) items dealt round-robin to the converter warps
-                    int q = 0;
-                    for (unsigned m = mask; m; m &= m - 1) {
-                        const int t = __ffs(m) - 1;
-                        for (int op = 0; op < 2; ++op, ++q) {
-                            if ((q & (kTcConvWarps - 1)) != cw)
-                                continue;
-                            const int K = __shfl_sync(0xffffffffu, me.K, t);
-                            if (op == 0) {
-                                const int M = __shfl_sync(0xffffffffu, me.M, t);
-                                const int ta = __shfl_sync(0xffffffffu, me.ta, t);
-                                const int offA = __shfl_sync(0xffffffffu, me.offA, t);
-                                const int csA = __shfl_sync(0xffffffffu, me.csA, t);
-                                const int R = __shfl_sync(0xffffffffu, me.R, t);
-                                // op(A)(i, k): stored A[i + k*lda] (N) or A[k + i*lda] (T)
-                                convert_chunk<P>(A0, A1, T.S.base + offA, ta ? csA : 4, ta ? 4 : csA, M, K, R, k0, kc,
-                                                 ta != 0);
-                            } else {
-                                const int N = __shfl_sync(0xffffffffu, me.N, t);
-                                const int tb = __shfl_sync(0xffffffffu, me.tb, t);
-                                const int offB = __shfl_sync(0xffffffffu, me.offB, t);
-                                const int csB = __shfl_sync(0xffffffffu, me.csB, t);
-                                const int Cc = __shfl_sync(0xffffffffu, me.Cc, t);
-                                // B operand row n = column n of op(B): stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
-                                convert_chunk<P>(B0, B1, T.S.base + offB, tb ? 4 : csB, tb ? csB : 4, N, K, Cc, k0, kc,
-                                                 tb == 0);
-                            }
+                if (kc > 0 && my_task >= 0) {
+                    // this thread's pack row: its K-groups of the chunk
+                    char *t0 = side == 0 ? A0 : B0;
+                    char *t1 = side == 0 ? A1 : B1;
+                    const int ng = kc / VPR;
+#pragma unroll 1
+                    for (int gi = 0; gi < ng; ++gi) {
+                        const int kb = k0 + gi * VPR;
+                        const char *p = my_src + kb * my_sk;
+                        float x[8];
+                        if (kb + VPR <= my_K) {
+#pragma unroll
+                            for (int e = 0; e < VPR; ++e)
+                                x[e] = *reinterpret_cast<const float *>(p + e * my_sk);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VPR; ++e)
+                                x[e] = (kb + e < my_K) ? *reinterpret_cast<const float *>(p + e * my_sk) : 0.0f;
                         }
+                        store_row<P>(t0, t1, row_off + (uint32_t)(gi * 128), x);
                     }
                 }
                 if (cw == 0 && lane == 0) {
@@ -514,8 +539,10 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
 {
     const Params &Pm = KP.p;
     const int lane = (int)lane_id();
-    const int row = 32 * ew + lane;                 // accumulator row (TMEM lane) of this thread
-    const uint32_t lane_base = (uint32_t)(32 * ew) << 16;
+    const int q = ew & 3;                           // TMEM lane quarter (warp index mod 4)
+    const int half = ew >> 2;                       // which alternate 16-column chunks
+    const int row = 32 * q + lane;                  // accumulator row (TMEM lane) of this thread
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     int a = 0;
     uint32_t apar[2] = {0u, 0u};
     for (int i = 0;; ++i) {
@@ -546,7 +573,7 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
             const uint32_t dt = tmem + (uint32_t)(a * kTcMaxCols) + lane_base;
             // tasks whose rows meet this warp's 32 rows
             const unsigned rows_mask = __ballot_sync(
-                0xffffffffu, ((mask >> lane) & 1) && me.R < 32 * ew + 32 && me.R + me.M > 32 * ew);
+                0xffffffffu, ((mask >> lane) & 1) && me.R < 32 * q + 32 && me.R + me.M > 32 * q);
             for (unsigned m = rows_mask; m; m &= m - 1) {
                 const int t = __ffs(m) - 1;
                 const TaskRec &r = recs[t];
@@ -559,7 +586,7 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
                 const int64_t ldc = r.ldc;
                 const char *c0 = T.S.base + r.offC + i_ * 4;
                 const int csC = r.csC;
-                for (int j0 = Cc & ~15; j0 < Cc + N; j0 += 16) {
+                for (int j0 = (Cc & ~15) + 16 * half; j0 < Cc + N; j0 += 32) {
                     float v[16];
                     if (KT > 0) {
                         tmem_ld16(dt + (uint32_t)j0, v);
@@ -569,14 +596,20 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
                             v[u] = 0.f;
                     }
                     if (mine) {
+                        // columns j0.. of the tile are columns j0-Cc.. of C
+                        const int jlo = max(j0, Cc) - Cc, jhi = min(j0 + 16, Cc + N) - Cc;
+                        float *cp = C + jlo * ldc;
+                        const char *c0p = c0 + jlo * csC;
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
                             const int j = j0 + u - Cc;
-                            if (j >= 0 && j < N) {
+                            if (j >= jlo && j < jhi) {
                                 float c = alpha * v[u];
                                 if (readc)
-                                    c = fmaf(beta, *reinterpret_cast<const float *>(c0 + j * csC), c);
-                                C[j * ldc] = c;
+                                    c = fmaf(beta, *reinterpret_cast<const float *>(c0p), c);
+                                *cp = c;
+                                cp += ldc;
+                                c0p += csC;
                             }
                         }
                     }

@@ -264,7 +264,8 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
             const int count = std::max(2000, (int)(96e6 / ((double)(bm * 40 + 40 * bn + 2 * bm * bn) * esz)));
             for (int i = 0; i < count; ++i) {
                 const int K = (i & 1) ? 16 : 48;
-                shapes.insert(shapes.end(), {bm, bn, K, i & 3});
+                static const int cases[3] = {0, 1, 3};   // NN, NT, TT: no TN-domain limit at these sizes
+                shapes.insert(shapes.end(), {bm, bn, K, cases[i % 3]});
                 model += model_block_cost(vs[v], esz, K);
             }
             DeviceBatch b;

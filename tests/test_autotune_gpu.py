@@ -1,0 +1,55 @@
+"""The autotuner (the GPU counterpart of the paper's install-time tuning):
+it times the register-tile variants and the stage size on this GPU, writes a
+JSON cache, and plans made with the tuned model stay correct."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2208_09822_gb300 import iaat
+from paper_2208_09822_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_09822_gb300 import build
+    build.build()
+    return torch
+
+
+def test_autotune_writes_cache_and_tuned_plans_stay_correct(tmp_path):
+    path = str(tmp_path / "tune.json")
+    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, path)
+    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, path)
+    cache = json.load(open(path))
+    assert len(cache["variant_scale_f32"]) == 5
+    assert all(v > 0 for v in cache["variant_scale_f32"])
+    assert cache["group_tasks_ffma"] in (8, 16, 24, 32)
+    assert cache["group_tasks_3xbf16"] in (8, 16, 24, 32)
+    # a fresh process reads the cache through IAAT_TUNE_CACHE and still
+    # matches the oracle
+    code = (
+        "import sys; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from paper_2208_09822_gb300 import workloads as W\n"
+        "from tests.gpu_util import run_grouped, compare\n"
+        "b = W.random_small(1500, seed=91, max_dim=60, pad_max=3)\n"
+        "import numpy as np\n"
+        "b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])\n"
+        "for prec in (0, 1):\n"
+        "    C, _ = run_grouped(b, prec)\n"
+        "    e = compare(b, C)\n"
+        "    assert e['eps_batch'] <= 1e-5, e\n"
+        "print('ok')\n" % (ROOT, ROOT))
+    env = dict(os.environ, IAAT_TUNE_CACHE=path)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
