@@ -134,10 +134,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_baseline_leg(batch, gpu_result, min_seconds):
+def cpu_baseline_leg(batch, gpu_results, min_seconds):
     """The CPU-baseline leg: time the FP64 oracle over the whole batch
     (repeated until min_seconds), and use its result to measure the error of
-    the GPU's first launch."""
+    each path's first launch."""
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from gpu_util import errors
@@ -152,9 +152,12 @@ def cpu_baseline_leg(batch, gpu_result, min_seconds):
     dt = time.perf_counter() - t0
     cpu = {"value": flops * reps / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
            "sample": f"the whole batch, {reps} pass(es) in {dt:.1f} s, FP64 triple loop"}
-    err = errors(batch, gpu_result, ref)
-    err["against"] = "FP64 oracle, all instances of the first launch"
-    return cpu, err
+    errs = {}
+    for name, res in gpu_results.items():
+        e = errors(batch, res, ref)
+        errs[name] = {k: e[k] for k in ("eps_batch", "eps_inst_max", "eps_inst_median", "eps_inst_rms")}
+        errs[name]["within_1e-5"] = e["eps_batch"] <= 1e-5
+    return cpu, errs
 
 
 def run_reference(args):
@@ -198,7 +201,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
-    ap.add_argument("--precision", default="ffma", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="3xbf16", choices=sorted(PRECISIONS),
+                    help="the headline path (the tensor-core FP32 split by default)")
+    ap.add_argument("--compare", default="ffma", type=lambda v: [x for x in v.split(",") if x],
+                    help="comma-separated paths timed beside the headline (plain FP32 by default)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=200_000,
@@ -226,55 +232,65 @@ def main():
     from paper_2208_09822_gb300 import workloads as W
 
     batch = W.uneven(count=args.instances)
-    prec = PRECISIONS[args.precision]
     tA = torch.from_numpy(batch.A).to(dev)
     tB = torch.from_numpy(batch.B).to(dev)
     tC = torch.from_numpy(batch.C).to(dev)
     C0 = tC.clone()
     descs = iaat.descs_for_pools(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
-    plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, prec)
-    info = iaat.iaat_plan_info(plan)
     stream = torch.cuda.Stream(device=dev)
 
-    # first launch; its result is checked against the oracle in the CPU leg
-    with torch.cuda.stream(stream):
-        iaat.iaat_gemm_grouped(plan, stream)
-    iaat.iaat_plan_check(plan, stream)
-    first_result = tC.cpu().numpy() if rank == 0 else None
+    def time_path(name):
+        """First launch (kept for the error check), then a CUDA graph of one
+        launch replayed `steps` times between events on the launch stream."""
+        plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, PRECISIONS[name])
+        info = iaat.iaat_plan_info(plan)
+        tC.copy_(C0)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            iaat.iaat_gemm_grouped(plan, stream)
+        iaat.iaat_plan_check(plan, stream)
+        first = tC.cpu().numpy() if rank == 0 else None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            iaat.iaat_gemm_grouped(plan, stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):   # replay() launches on the current stream
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        iaat.iaat_plan_check(plan, stream)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return plan, info, ms, first
 
-    # graph of one launch, replayed
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        iaat.iaat_gemm_grouped(plan, stream)
-    tC.copy_(C0)
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            g.replay()
-    torch.cuda.synchronize()
+    # the compared paths first, then the headline path with the clock sampler
+    others = [p for p in args.compare if p != args.precision]
+    results = {}
+    for name in others:
+        plan_o, info_o, ms_o, first_o = time_path(name)
+        results[name] = (info_o, ms_o, first_o)
+        plan_o.destroy()
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.25)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):   # replay() launches on the current stream
-        e0.record(stream)
-        for _ in range(args.steps):
-            g.replay()
-        e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    plan, info, ms, first_result = time_path(args.precision)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    iaat.iaat_plan_check(plan, stream)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    results[args.precision] = (info, ms, first_result)
 
     flops = info["flops"]
     value = flops * world / (ms * 1e-3) / 1e9
@@ -319,15 +335,22 @@ def main():
     e2e_value = flops * world / (e2e_ms * 1e-3) / 1e9
 
     if rank == 0:
-        cpu, err = None, None
+        cpu, errs = None, {}
         if world == 1 and not args.no_cpu_baseline:
-            cpu, err = cpu_baseline_leg(batch, first_result, 10.0)
+            cpu, errs = cpu_baseline_leg(batch, {k: v[2] for k, v in results.items()}, 10.0)
         traffic = profile_traffic(args.precision)
+        paths = {}
+        for name, (inf, ms_p, _) in results.items():
+            paths[name] = {"value": inf["flops"] * world / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
+                           "ms_per_step": ms_p,
+                           "roofline_frac": inf["algorithmic_bytes"] / (ms_p * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                           "error": errs.get(name)}
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(n=batch.count), "instances": batch.count, "precision": args.precision,
+            "config": {"workload": WORKLOAD.format(n=batch.count), "instances": batch.count,
+                       "precision": args.precision,
                        "parallelism": f"instances x{world} (one batch per GPU)",
                        "l2": "inputs larger than L2 (pools %.2f GB > 129 MB); no flush" %
                              ((batch.A.nbytes + batch.B.nbytes + batch.C.nbytes) / 1e9),
@@ -342,9 +365,10 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "paths": paths,
+            "error": errs.get(args.precision),
             "gpu_launches": args.steps * info["kernels"],
             "clocks": clocks,
-            "error": err,
         }
         print(json.dumps(line), flush=True)
     plan.destroy()

@@ -87,13 +87,41 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
     int oldest = 0;
     int i = 0;
     bool failed = false;
+    // Descriptor loads run ahead of the stage being issued: the stage index
+    // of stage i+2 and the task descriptors of stage i+1 are in flight while
+    // stage i is sized and its copies issued, so the two dependent global
+    // reads per stage do not sit on the producer's critical path.
+    auto load_bounds = [&](int ii, int &b0, int &b1) {
+        const int gg = sched_group(ii, blockIdx.x, gridDim.x);
+        if (gg < P.ngroups) {
+            b0 = gbeg[gg];
+            b1 = gbeg[gg + 1];
+        } else {
+            b0 = b1 = 0;
+        }
+    };
+    auto load_desc = [&](int b0, int b1, TaskDesc &d) {
+        const int nt = b1 - b0;
+        if ((int)lane < nt && nt <= kMaxGroupTasks) {
+            d = tasks[b0 + lane];
+        } else {
+            d.A = d.B = nullptr; d.C = nullptr;
+            d.lda = d.ldb = d.ldc = 1; d.M = d.N = d.K = 0; d.ta = d.tb = 0;
+            d.variant = 0; d.flags = 0; d.nbm = d.nbn = 1; d.alpha = d.beta = 0.0;
+        }
+    };
+    int cb0, cb1, nb0, nb1;
+    load_bounds(0, cb0, cb1);
+    load_bounds(1, nb0, nb1);
+    TaskDesc d_cur;
+    load_desc(cb0, cb1, d_cur);
     for (;; ++i) {
         const int g = sched_group(i, blockIdx.x, gridDim.x);
         if (g >= P.ngroups)
             break;
         const int slot = i % kNumSlots;
-        const int t0 = gbeg[g];
-        const int nt = gbeg[g + 1] - t0;
+        const int t0 = cb0;
+        const int nt = cb1 - cb0;
         if (nt < 0 || nt > kMaxGroupTasks) {
             if (lane == 0)
                 set_error(P.err, kErrBadGroup);
@@ -101,14 +129,13 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
             break;
         }
         const bool has = (int)lane < nt;
-        TaskDesc d;
-        if (has)
-            d = tasks[t0 + lane];
-        else {
-            d.A = d.B = nullptr; d.C = nullptr;
-            d.lda = d.ldb = d.ldc = 1; d.M = d.N = d.K = 0; d.ta = d.tb = 0;
-            d.variant = 0; d.flags = 0; d.nbm = d.nbn = 1; d.alpha = d.beta = 0.0;
-        }
+        const TaskDesc d = d_cur;
+        (void)t0;
+        // prefetch: descriptors of stage i+1, bounds of stage i+2
+        load_desc(nb0, nb1, d_cur);
+        cb0 = nb0;
+        cb1 = nb1;
+        load_bounds(i + 2, nb0, nb1);
         TaskStages st = plan_task(d, ESZ);
         const uint32_t f = has ? st.total() : 0u;
         const uint32_t tx = has ? (st.a.tx + st.b.tx + st.c.tx) : 0u;
