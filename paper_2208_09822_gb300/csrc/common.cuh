@@ -185,8 +185,9 @@ template <> struct Traits<8> {
 };
 
 // Shared-memory map of the persistent kernel (byte offsets).
-constexpr int kSmemBarriers = 0;                          // full[], empty[]
-constexpr int kSmemSlots = 256;
+constexpr int kSmemBarriers = 0;                          // full[], empty[], ring ranges
+constexpr int kSmemTaskBars = 256;                        // per-task readiness [slot][task]
+constexpr int kSmemSlots = kSmemTaskBars + kNumSlots * kMaxGroupTasks * 8;
 constexpr int kSmemCanon = kSmemSlots + kNumSlots * kSlotBytes;
 template <int ESZ> IAAT_CE int smem_ring_offset()
 {

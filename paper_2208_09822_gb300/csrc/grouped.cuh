@@ -38,7 +38,11 @@ struct SmemMap {
     uint32_t sbase;
     uint32_t ring_off;     // byte offset of the staging ring from base
     uint32_t ring_bytes;   // its size
+    // full(s): the stage's records are published; task(s, t): the operands
+    // of task t of the stage have landed (one barrier per task, so consumers
+    // start on the first tasks of a stage while later ones are in flight).
     __device__ uint32_t full(int s) const { return sbase + kSmemBarriers + 8 * s; }
+    __device__ uint32_t task(int s, int t) const { return sbase + kSmemTaskBars + 8 * (s * kMaxGroupTasks + t); }
     __device__ uint32_t empty(int s) const { return sbase + kSmemBarriers + 64 + 8 * s; }
     __device__ uint32_t *range_beg() const { return reinterpret_cast<uint32_t *>(base + 128); }
     __device__ uint32_t *range_end() const { return reinterpret_cast<uint32_t *>(base + 160); }
@@ -140,7 +144,7 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
         const uint32_t f = has ? st.total() : 0u;
         const uint32_t tx = has ? (st.a.tx + st.b.tx + st.c.tx) : 0u;
         const int nb = has ? (int)d.nbm * (int)d.nbn : 0;
-        uint32_t incl = f, txs = tx;
+        uint32_t incl = f;
         int nbi = nb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -150,7 +154,6 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
                 incl += v;
                 nbi += w;
             }
-            txs += __shfl_xor_sync(0xffffffffu, txs, o);
         }
         const uint32_t F = __shfl_sync(0xffffffffu, incl, 31);
         const int NB = __shfl_sync(0xffffffffu, nbi, 31);
@@ -211,12 +214,15 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
         }
         __syncwarp();
         if (lane == 0)
-            mbar_arrive_expect_tx(S.full(slot), txs);
-        __syncwarp();
+            mbar_arrive(S.full(slot));
+        // every lane arms its task's barrier (no bytes for lanes without a
+        // task, so all 32 complete once per use of the slot), then issues
+        // that task's copies
+        mbar_arrive_expect_tx(S.task(slot, (int)lane), tx);
         if (has) {
             int ha, wa, hb, wb;
             stored_dims(d, ha, wa, hb, wb);
-            const uint32_t bar = S.full(slot);
+            const uint32_t bar = S.task(slot, (int)lane);
             const uint32_t dst = S.sbase + base;
             const bool prod = d.K > 0;
             issue_stage(st.a, d.A, prod ? ha : 0, prod ? wa : 0, d.lda, ESZ, dst, bar);
@@ -226,10 +232,10 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
     }
     // Copies still in flight target this CTA's shared memory: before leaving,
     // wait (bounded) until every issued stage has landed.
-    if (lane == 0) {
+    {
         const int first = i - kNumSlots > 0 ? i - kNumSlots : 0;
         for (int s = first; s < i; ++s)
-            if (!mbar_wait(S.full(s % kNumSlots), (uint32_t)((s / kNumSlots) & 1), kWaitLimitNs))
+            if (!mbar_wait(S.task(s % kNumSlots, (int)lane), (uint32_t)((s / kNumSlots) & 1), kWaitLimitNs))
                 set_error(P.err, kErrTimeoutFull);
     }
     (void)failed;
@@ -476,6 +482,11 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
             const int t = __popc(__ballot_sync(0xffffffffu, pre <= b));
             const int before = __shfl_sync(0xffffffffu, pre, t > 0 ? t - 1 : 0);
             const int lb = b - (t > 0 ? before : 0);
+            if (!mbar_wait(S.task(slot, t), (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs)) {
+                if (lane == 0)
+                    set_error(P.err, kErrTimeoutFull);
+                return;
+            }
             const TaskRec r = recs[t];
             const int bi = lb % r.nbm, bj = lb / r.nbm;
             dispatch_block<T>(S.base, r, bi, bj, As, Bs);
@@ -496,13 +507,15 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
     S.ring_off = (uint32_t)smem_ring_offset<(int)sizeof(T)>();
     S.ring_bytes = (uint32_t)ring_bytes<(int)sizeof(T)>();
     const int warp = threadIdx.x / 32;
+    if (threadIdx.x < kNumSlots * kMaxGroupTasks)
+        mbar_init(S.task(threadIdx.x / kMaxGroupTasks, threadIdx.x % kMaxGroupTasks), 1);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNumSlots; ++s) {
             mbar_init(S.full(s), 1);
             mbar_init(S.empty(s), kConsumerWarps);
         }
-        fence_barrier_init();
     }
+    fence_barrier_init();
     __syncthreads();
     if (warp == kConsumerWarps)
         producer_loop<(int)sizeof(T)>(KP, S);

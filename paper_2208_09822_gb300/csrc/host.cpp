@@ -343,13 +343,11 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int fo
 
 // Order tasks by cost (largest first) and cut them into stages of at most
 // max_tasks tasks and `cap` bytes of shared memory (half the staging ring, so
-// two stages always fit).  A stage is closed once it holds cap/2 bytes, so
-// that about four stages are in flight per SM; a task larger than that
-// travels in a stage of its own.
+// two stages always fit).  Each task of a stage has its own readiness
+// barrier, so a large stage still lets the consumers start early.
 void make_groups(std::vector<HostTask> &tasks, uint32_t cap, int max_tasks, std::vector<TaskDesc> &flat,
                  std::vector<int32_t> &gbeg)
 {
-    cap = cap / 2;
     std::stable_sort(tasks.begin(), tasks.end(),
                      [](const HostTask &a, const HostTask &b) { return a.cost > b.cost; });
     flat.clear();
@@ -764,7 +762,7 @@ iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, i
     int64_t ng = 0;
     uint32_t used = 0;
     int in_group = 0;
-    const uint32_t target = cap / 2;   // the regular planner's stage size
+    const uint32_t target = cap;   // the regular planner's stage size
     for (int64_t k = 0; k < nt; ++k) {
         const int32_t t = order[k];
         if (in_group == 0 || in_group >= group_tasks || used + bytes[t] > target) {

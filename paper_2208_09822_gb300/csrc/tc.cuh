@@ -384,6 +384,18 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
             const int my_sk = kcontig ? 4 : t_cs;
             const char *my_src = T.S.base + t_off + (row - t_lo) * my_si;
             const uint32_t row_off = (uint32_t)((row >> 3) * tc_sbo<P>() + (row & 7) * 16);
+            // this row's operand bytes must have landed (each thread acquires
+            // the barrier of its own task)
+            {
+                const bool ok = my_task < 0 || mbar_wait(T.S.task(slot, my_task),
+                                                         (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0)
+                        set_error(Pm.err, kErrTimeoutFull);
+                    alive = false;
+                    break;
+                }
+            }
             for (int c = 0; c < nch; ++c) {
                 // the MMAs that read this stage one round ago must be done
                 if (uses >= kTcStages && !warp_wait(T.op_empty(b), bpar ^ 1u)) {
@@ -579,6 +591,9 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
                 const TaskRec &r = recs[t];
                 const int R = r.nbm, M = r.M, Cc = r.nbn, N = r.N;
                 const bool mine = row >= R && row < R + M;
+                if (mine && (r.flags & kFlagReadC) &&
+                    !mbar_wait(T.S.task(slot, t), (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs))
+                    set_error(Pm.err, kErrTimeoutFull);
                 const int i_ = mine ? row - R : 0;
                 const float alpha = (float)r.alpha, beta = (float)r.beta;
                 const bool readc = (r.flags & kFlagReadC) != 0;
@@ -637,6 +652,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
     T.S.ring_off = (uint32_t)tc_ring_offset<P>();
     T.S.ring_bytes = (uint32_t)tc_ring_bytes<P>();
     const int warp = threadIdx.x / 32;
+    if (threadIdx.x < kNumSlots * kMaxGroupTasks)
+        mbar_init(T.S.task(threadIdx.x / kMaxGroupTasks, threadIdx.x % kMaxGroupTasks), 1);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNumSlots; ++s) {
             mbar_init(T.S.full(s), 1);
