@@ -26,8 +26,7 @@ namespace iaat {
 constexpr int kMaxDim = 80;          // cbrt(MNK) <= 80 bounds every size used here
 constexpr int kMaxGroupTasks = 32;   // tasks per pipeline stage (one per producer lane)
 constexpr int kNumSlots = 8;         // pipeline stages in flight per CTA
-constexpr int kConsumerWarps = 8;    // compute warps per CTA
-constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+constexpr int kConsumerWarps = 8;    // compute warps per CTA (FP64; FP32 uses Traits<4>::kWarps)
 
 // One piece of work: a whole instance, or a column range of it.  Pointers
 // address element (0,0) of the piece's stored A, B, C.  64 bytes.
@@ -175,14 +174,20 @@ constexpr int kMaxBM = 32, kMaxBN = 32;  // largest warp block over both familie
 
 // Per-warp canonical operand buffers: As[KC][BM], Bs[KC][BN].
 template <int ESZ> struct Traits;
+// kWarps: consumer warps per CTA (one more warp is the producer).  FP32 runs
+// 16 so each scheduler has four warps to hide shared-memory latency with;
+// FP64 keeps 8 because its register tiles need twice the registers.
 template <> struct Traits<4> {
     static constexpr int KC = kKC;
     static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 4;   // 4 KB
+    static constexpr int kWarps = 16;
 };
 template <> struct Traits<8> {
     static constexpr int KC = kKC64;
     static constexpr int kCanonBytes = KC * (kMaxBM + kMaxBN) * 8;   // 4 KB
+    static constexpr int kWarps = kConsumerWarps;
 };
+template <int ESZ> IAAT_CE int kernel_threads() { return 32 * (Traits<ESZ>::kWarps + 1); }
 
 // Shared-memory map of the persistent kernel (byte offsets).
 constexpr int kSmemBarriers = 0;                          // full[], empty[], ring ranges
@@ -191,7 +196,7 @@ constexpr int kSmemSlots = kSmemTaskBars + kNumSlots * kMaxGroupTasks * 8;
 constexpr int kSmemCanon = kSmemSlots + kNumSlots * kSlotBytes;
 template <int ESZ> IAAT_CE int smem_ring_offset()
 {
-    return ((kSmemCanon + kConsumerWarps * Traits<ESZ>::kCanonBytes) + 127) & ~127;
+    return ((kSmemCanon + Traits<ESZ>::kWarps * Traits<ESZ>::kCanonBytes) + 127) & ~127;
 }
 constexpr int kSmemTotal = 227 * 1024;
 template <int ESZ> IAAT_CE int ring_bytes() { return (kSmemTotal - smem_ring_offset<ESZ>()) & ~127; }

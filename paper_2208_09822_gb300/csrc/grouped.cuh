@@ -478,7 +478,7 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
         const TaskRec *recs = S.recs(slot);
         const int nb = hd->nblocks;
         const int pre = hd->prefix[lane];
-        for (int b = warp; b < nb; b += kConsumerWarps) {
+        for (int b = warp; b < nb; b += Traits<ESZ>::kWarps) {
             const int t = __popc(__ballot_sync(0xffffffffu, pre <= b));
             const int before = __shfl_sync(0xffffffffu, pre, t > 0 ? t - 1 : 0);
             const int lb = b - (t > 0 ? before : 0);
@@ -498,8 +498,9 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_constant__ KParams KP)
+__global__ void __launch_bounds__(kernel_threads<(int)sizeof(T)>(), 1) grouped_kernel(const __grid_constant__ KParams KP)
 {
+    constexpr int kWarps = Traits<(int)sizeof(T)>::kWarps;
     extern __shared__ __align__(128) char smem[];
     SmemMap S;
     S.base = smem;
@@ -512,12 +513,12 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNumSlots; ++s) {
             mbar_init(S.full(s), 1);
-            mbar_init(S.empty(s), kConsumerWarps);
+            mbar_init(S.empty(s), kWarps);
         }
     }
     fence_barrier_init();
     __syncthreads();
-    if (warp == kConsumerWarps)
+    if (warp == kWarps)
         producer_loop<(int)sizeof(T)>(KP, S);
     else
         consumer_loop<T>(KP, S, warp);

@@ -24,9 +24,9 @@ cudaError_t launch_fma(int dtype, const KParams &kp, int grid, cudaStream_t stre
     if (grid <= 0)
         return cudaSuccess;
     if (dtype == 0)
-        grouped_kernel<float><<<grid, kThreads, kSmemTotal, stream>>>(kp);
+        grouped_kernel<float><<<grid, kernel_threads<4>(), kSmemTotal, stream>>>(kp);
     else
-        grouped_kernel<double><<<grid, kThreads, kSmemTotal, stream>>>(kp);
+        grouped_kernel<double><<<grid, kernel_threads<8>(), kSmemTotal, stream>>>(kp);
     return cudaGetLastError();
 }
 
