@@ -105,7 +105,7 @@ typedef struct {
     int64_t active;            /* instances that need work */
     int64_t tasks;             /* work pieces after splitting */
     int64_t groups;            /* pipeline stages */
-    int64_t blocks;            /* warp blocks over all tasks */
+    int64_t blocks;            /* warp blocks over all tasks (tensor-core plans: MMA packs) */
     int64_t flops;             /* sum of 2*M*N*K over active instances (Eq. 1) */
     int64_t algorithmic_bytes; /* A, B, C written, C read when beta != 0 */
     int64_t plan_bytes;        /* device bytes the plan holds (descriptors) */

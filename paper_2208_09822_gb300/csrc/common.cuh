@@ -58,10 +58,22 @@ struct alignas(16) TaskRec {
 };
 static_assert(sizeof(TaskRec) == 64, "TaskRec layout");
 
+// Tensor-core kernel: one pack (one 128-row MMA tile) of a stage, as the
+// producer summarises it for the converter, MMA and epilogue roles.
+struct alignas(16) PackInfo {
+    int8_t qtask[4];   // task owning each 32-row quarter of the tile (-1: none)
+    int8_t btask[8];   // task owning each 16-column block (-1: none)
+    int16_t kmax;      // largest K of the pack's tasks
+    uint8_t nt;        // MMA N: end of the last task's 16-column blocks (>= 16)
+    uint8_t pad;
+};
+static_assert(sizeof(PackInfo) == 16, "PackInfo layout");
+
 struct alignas(16) SlotHeader {
     int32_t ntasks;
     int32_t nblocks;
-    int32_t pad[2];
+    int32_t npacks;   // tensor-core kernel: packs of the stage
+    int32_t pad;
     int32_t prefix[kMaxGroupTasks];  // inclusive prefix of blocks per task
 };
 constexpr int kSlotBytes = sizeof(SlotHeader) + kMaxGroupTasks * sizeof(TaskRec);
@@ -203,10 +215,47 @@ template <int ESZ> IAAT_CE int ring_bytes() { return (kSmemTotal - smem_ring_off
 // A stage may take at most half the ring, so two always fit.
 template <int ESZ> IAAT_CE int max_group_bytes() { return ring_bytes<ESZ>() / 2; }
 
+// Order in which the CTAs take the cost-sorted stages: stage i of CTA `cta`
+// is group sched_group(i, cta, ncta), a snake over the groups that balances
+// like LPT without atomics.
+IAAT_HD int sched_group(int i, int cta, int ncta)
+{
+    return i * ncta + ((i & 1) ? (ncta - 1 - cta) : cta);
+}
+
+// ------------------------------------------------------- stage programs
+// iaat_plan_create turns the plan into one program per stage, executed by the
+// producer warp of the CTA that runs the stage: everything about the stage
+// that does not change between launches -- where its operands go in the
+// staging ring, which earlier stage must release the space first, the task
+// records and pack summaries the consumers read, the bytes each readiness
+// barrier expects, and the list of bulk copies -- is computed once on the
+// host.  Program layout (16-byte aligned, at poff[g] for group g):
+//   StageProg | uint32 tx[32] | CopyCmd[ncmd] | SlotHeader + TaskRec[nt] | PackInfo[npk]
+struct alignas(16) StageProg {
+    int32_t wait;        // stage of this CTA's sequence that must be released first (-1: none)
+    uint32_t rec_bytes;  // SlotHeader + TaskRec[nt]: copied to the stage's slot
+    uint16_t ncmd;       // copy commands
+    uint8_t nt, npk;     // tasks, packs (tensor-core kernel: PackInfo[npk] follows the records)
+    uint32_t ctx;        // tensor-core kernel: bytes of the stage's C copies (one barrier)
+};
+static_assert(sizeof(StageProg) == 16, "StageProg layout");
+struct alignas(16) CopyCmd {
+    const char *src;     // 16-byte aligned global address
+    uint32_t dst;        // byte offset from the shared-memory base, 16-byte aligned
+    uint32_t meta;       // bytes (bits 0-23, a multiple of 16) | barrier << 24 (task t, or 32: C barrier)
+};
+static_assert(sizeof(CopyCmd) == 16, "CopyCmd layout");
+constexpr int kProgTx = 16;
+constexpr int kProgCmds = kProgTx + 4 * kMaxGroupTasks;
+constexpr uint32_t kCmdBarC = 32;
+
 // Kernel parameters.
 struct Params {
     const TaskDesc *tasks;
     const int32_t *gbeg;      // group g = tasks [gbeg[g], gbeg[g+1])
+    const char *prog;         // stage programs (plans); NULL: plan on the device
+    const int64_t *poff;      // program of group g at prog + poff[g]
     int32_t ngroups;
     int32_t pad;
     int32_t *err;             // device error word (0 = fine)

@@ -21,12 +21,6 @@ namespace iaat {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
 
-__device__ __forceinline__ int sched_group(int i, int cta, int ncta)
-{
-    // snake order over cost-sorted groups: balances like LPT without atomics
-    return i * ncta + ((i & 1) ? (ncta - 1 - cta) : cta);
-}
-
 __device__ __forceinline__ void set_error(int32_t *err, int32_t code)
 {
     if (err)
@@ -38,6 +32,8 @@ struct SmemMap {
     uint32_t sbase;
     uint32_t ring_off;     // byte offset of the staging ring from base
     uint32_t ring_bytes;   // its size
+    uint32_t pinfo_off;    // tensor-core kernel: PackInfo[kNumSlots][kMaxGroupTasks]
+    uint32_t cbar_off;     // tensor-core kernel: per-slot barrier of the C copies
     // full(s): the stage's records are published; task(s, t): the operands
     // of task t of the stage have landed (one barrier per task, so consumers
     // start on the first tasks of a stage while later ones are in flight).
@@ -46,6 +42,11 @@ struct SmemMap {
     __device__ uint32_t empty(int s) const { return sbase + kSmemBarriers + 64 + 8 * s; }
     __device__ uint32_t *range_beg() const { return reinterpret_cast<uint32_t *>(base + 128); }
     __device__ uint32_t *range_end() const { return reinterpret_cast<uint32_t *>(base + 160); }
+    __device__ PackInfo *pinfo(int s) const
+    {
+        return reinterpret_cast<PackInfo *>(base + pinfo_off) + s * kMaxGroupTasks;
+    }
+    __device__ uint32_t cfull(int s) const { return sbase + cbar_off + 8 * s; }
     __device__ SlotHeader *header(int s) const
     {
         return reinterpret_cast<SlotHeader *>(base + kSmemSlots + s * kSlotBytes);
@@ -77,8 +78,11 @@ __device__ __forceinline__ void issue_stage(const Stage &st, const char *p, int 
     }
 }
 
+// Producer of a plan launched without stage programs (the single-call and
+// allocation-free entry points, CUDA-core kernel): sizes each stage's tasks,
+// claims ring space and writes the records itself.  Lane t handles task t.
 template <int ESZ>
-__device__ void producer_loop(const KParams &KP, const SmemMap &S)
+__device__ void producer_dyn(const KParams &KP, const SmemMap &S)
 {
     const Params &P = KP.p;
     const TaskDesc *tasks = P.tasks ? P.tasks : KP.inline_tasks;
@@ -90,18 +94,15 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
     uint32_t head = 0;
     int oldest = 0;
     int i = 0;
-    bool failed = false;
     // Descriptor loads run ahead of the stage being issued: the stage index
     // of stage i+2 and the task descriptors of stage i+1 are in flight while
-    // stage i is sized and its copies issued, so the two dependent global
-    // reads per stage do not sit on the producer's critical path.
+    // stage i is sized and its copies issued.
     auto load_bounds = [&](int ii, int &b0, int &b1) {
         const int gg = sched_group(ii, blockIdx.x, gridDim.x);
+        b0 = b1 = 0;
         if (gg < P.ngroups) {
             b0 = gbeg[gg];
             b1 = gbeg[gg + 1];
-        } else {
-            b0 = b1 = 0;
         }
     };
     auto load_desc = [&](int b0, int b1, TaskDesc &d) {
@@ -124,18 +125,14 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
         if (g >= P.ngroups)
             break;
         const int slot = i % kNumSlots;
-        const int t0 = cb0;
         const int nt = cb1 - cb0;
         if (nt < 0 || nt > kMaxGroupTasks) {
             if (lane == 0)
                 set_error(P.err, kErrBadGroup);
-            failed = true;
             break;
         }
         const bool has = (int)lane < nt;
         const TaskDesc d = d_cur;
-        (void)t0;
-        // prefetch: descriptors of stage i+1, bounds of stage i+2
         load_desc(nb0, nb1, d_cur);
         cb0 = nb0;
         cb1 = nb1;
@@ -184,7 +181,6 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
         if (!ok) {
             if (lane == 0)
                 set_error(P.err, kErrTimeoutEmpty);
-            failed = true;
             break;
         }
         a = __shfl_sync(0xffffffffu, a, 0);
@@ -211,6 +207,7 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
         if (lane == 0) {
             hd->ntasks = nt;
             hd->nblocks = NB;
+            hd->npacks = 0;
         }
         __syncwarp();
         if (lane == 0)
@@ -232,13 +229,152 @@ __device__ void producer_loop(const KParams &KP, const SmemMap &S)
     }
     // Copies still in flight target this CTA's shared memory: before leaving,
     // wait (bounded) until every issued stage has landed.
-    {
-        const int first = i - kNumSlots > 0 ? i - kNumSlots : 0;
-        for (int s = first; s < i; ++s)
-            if (!mbar_wait(S.task(s % kNumSlots, (int)lane), (uint32_t)((s / kNumSlots) & 1), kWaitLimitNs))
-                set_error(P.err, kErrTimeoutFull);
+    const int first = i - kNumSlots > 0 ? i - kNumSlots : 0;
+    for (int s = first; s < i; ++s)
+        if (!mbar_wait(S.task(s % kNumSlots, (int)lane), (uint32_t)((s / kNumSlots) & 1), kWaitLimitNs))
+            set_error(P.err, kErrTimeoutFull);
+}
+
+// Producer of a plan with stage programs: per stage it waits for the release
+// the program names, copies the precomputed records (and, TC, the pack
+// summaries) into the slot on its full barrier, arms the readiness barriers
+// and issues the program's bulk copies.  TC: the stage feeds the tensor-core
+// kernel, whose C copies complete on the slot's cfull barrier (the epilogue
+// reads C long after the operands, so one wait per stage serves it).
+// The programs of the next stages are loaded ahead: the offset of stage
+// i+3, the header of stage i+2, and the barrier bytes and first 64 copy
+// commands of stage i+1 are in flight while stage i is issued.
+template <int ESZ, bool TC>
+__device__ void producer_prog(const KParams &KP, const SmemMap &S)
+{
+    const Params &P = KP.p;
+    const int lane = (int)lane_id();
+    const uint32_t lo = S.ring_off, hi = S.ring_off + S.ring_bytes;
+    auto prog_off = [&](int ii) -> int64_t {
+        const int gg = sched_group(ii, blockIdx.x, gridDim.x);
+        return gg < P.ngroups ? P.poff[gg] : (int64_t)-1;
+    };
+    auto load_hdr = [&](int64_t off) -> uint4 {
+        return off >= 0 ? *reinterpret_cast<const uint4 *>(P.prog + off) : make_uint4(0u, 0u, 0u, 0u);
+    };
+    struct Body {
+        uint32_t tx;
+        uint4 c0, c1;
+    };
+    auto load_body = [&](int64_t off, const uint4 &h, Body &b) {
+        b.tx = 0u;
+        b.c0 = b.c1 = make_uint4(0u, 0u, 0u, 0u);
+        if (off < 0)
+            return;
+        const int ncmd = (int)(h.z & 0xffffu);
+        b.tx = reinterpret_cast<const uint32_t *>(P.prog + off + kProgTx)[lane];
+        const uint4 *cm = reinterpret_cast<const uint4 *>(P.prog + off + kProgCmds);
+        if (lane < ncmd)
+            b.c0 = cm[lane];
+        if (lane + 32 < ncmd)
+            b.c1 = cm[lane + 32];
+    };
+    int64_t off_c = prog_off(0), off_n = prog_off(1), off_nn = prog_off(2);
+    uint4 h_c = load_hdr(off_c), h_n = load_hdr(off_n);
+    Body b_c;
+    load_body(off_c, h_c, b_c);
+    int oldest = 0;
+    int i = 0;
+    bool bad = false;
+    for (;; ++i) {
+        if (off_c < 0)
+            break;
+        const int slot = i % kNumSlots;
+        const int wait = (int)h_c.x;
+        const uint32_t rec_bytes = h_c.y;
+        const int ncmd = (int)(h_c.z & 0xffffu);
+        const int nt = (int)((h_c.z >> 16) & 0xffu), npk = (int)(h_c.z >> 24);
+        const uint32_t ctx = h_c.w;
+        const char *pg = P.prog + off_c;
+        const Body b = b_c;
+        // loads for the next stages
+        load_body(off_n, h_n, b_c);
+        const uint4 h_nn = load_hdr(off_nn);
+        const int64_t off_nnn = prog_off(i + 3);
+        if (nt > kMaxGroupTasks || npk > kMaxGroupTasks || wait >= i ||
+            rec_bytes != (uint32_t)(sizeof(SlotHeader) + nt * sizeof(TaskRec)) || (!TC && npk != 0)) {
+            if (lane == 0)
+                set_error(P.err, kErrBadGroup);
+            bad = true;
+            break;
+        }
+        // the release that frees this stage's slot and ring space
+        int ok = 1;
+        if (lane == 0 && wait >= oldest) {
+            ok = mbar_wait(S.empty(wait % kNumSlots), (uint32_t)((wait / kNumSlots) & 1), kWaitLimitNs) ? 1 : 0;
+            oldest = wait + 1;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0)
+                set_error(P.err, kErrTimeoutEmpty);
+            bad = true;
+            break;
+        }
+        if (lane == 0) {
+            const uint32_t pkb = (uint32_t)npk * (uint32_t)sizeof(PackInfo);
+            mbar_arrive_expect_tx(S.full(slot), rec_bytes + pkb);
+            const char *img = pg + kProgCmds + ncmd * (int)sizeof(CopyCmd);
+            bulk_g2s(smem_addr(S.header(slot)), img, rec_bytes, S.full(slot));
+            if (TC && npk > 0)
+                bulk_g2s(smem_addr(S.pinfo(slot)), img + rec_bytes, pkb, S.full(slot));
+            if (TC)
+                mbar_arrive_expect_tx(S.cfull(slot), ctx);
+        }
+        __syncwarp();
+        // every lane arms its task's barrier (0 bytes without a task, so all
+        // 32 complete once per use of the slot)
+        mbar_arrive_expect_tx(S.task(slot, lane), b.tx);
+        __syncwarp();
+        auto issue = [&](const uint4 &c) {
+            const uint32_t bytes = c.w & 0xffffffu, bar = c.w >> 24;
+            if (c.z < lo || c.z + bytes > hi || ((c.z | bytes | c.x) & 15u) != 0u || bar > (TC ? kCmdBarC : 31u)) {
+                set_error(P.err, kErrBadGroup);
+                return;
+            }
+            const char *src = reinterpret_cast<const char *>(((uint64_t)c.y << 32) | c.x);
+            bulk_g2s(S.sbase + c.z, src, bytes, bar == kCmdBarC ? S.cfull(slot) : S.task(slot, (int)bar));
+        };
+        if (lane < ncmd)
+            issue(b.c0);
+        if (lane + 32 < ncmd)
+            issue(b.c1);
+        const uint4 *cm = reinterpret_cast<const uint4 *>(pg + kProgCmds);
+        for (int k = lane + 64; k < ncmd; k += 32)
+            issue(cm[k]);
+        off_c = off_n;
+        h_c = h_n;
+        off_n = off_nn;
+        h_n = h_nn;
+        off_nn = off_nnn;
     }
-    (void)failed;
+    (void)bad;
+    // Copies still in flight target this CTA's shared memory: before leaving,
+    // wait (bounded) until every issued stage has landed.
+    const int first = i - kNumSlots > 0 ? i - kNumSlots : 0;
+    for (int s = first; s < i; ++s) {
+        const uint32_t par = (uint32_t)((s / kNumSlots) & 1);
+        if (!mbar_wait(S.task(s % kNumSlots, lane), par, kWaitLimitNs) ||
+            !mbar_wait(S.full(s % kNumSlots), par, kWaitLimitNs) ||
+            (TC && !mbar_wait(S.cfull(s % kNumSlots), par, kWaitLimitNs)))
+            set_error(P.err, kErrTimeoutFull);
+    }
+}
+
+template <int ESZ, bool TC = false>
+__device__ void producer_loop(const KParams &KP, const SmemMap &S)
+{
+    if (KP.p.prog)
+        producer_prog<ESZ, TC>(KP, S);
+    else if constexpr (!TC)
+        producer_dyn<ESZ>(KP, S);
+    else if (lane_id() == 0)
+        set_error(KP.p.err, kErrBadGroup);   // tensor-core launches always carry programs
 }
 
 // Position of element m of canonical row kk: 16-byte groups XOR-swizzled by
@@ -507,6 +643,8 @@ __global__ void __launch_bounds__(kernel_threads<(int)sizeof(T)>(), 1) grouped_k
     S.sbase = smem_addr(smem);
     S.ring_off = (uint32_t)smem_ring_offset<(int)sizeof(T)>();
     S.ring_bytes = (uint32_t)ring_bytes<(int)sizeof(T)>();
+    S.pinfo_off = 0;
+    S.cbar_off = 0;
     const int warp = threadIdx.x / 32;
     if (threadIdx.x < kNumSlots * kMaxGroupTasks)
         mbar_init(S.task(threadIdx.x / kMaxGroupTasks, threadIdx.x % kMaxGroupTasks), 1);

@@ -228,8 +228,8 @@ struct iaat_plan_s {
     int esz = 4;
     iaat_dtype_t dtype = IAAT_F32;
     iaat_precision_t precision = IAAT_PREC_DEFAULT;
-    TaskDesc *d_tasks = nullptr;
-    int32_t *d_gbeg = nullptr;
+    char *d_prog = nullptr;        // stage programs
+    int64_t *d_poff = nullptr;     // program offset per group
     int32_t *d_err = nullptr;
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
@@ -278,9 +278,86 @@ int sm_count(int dev)
     return n;
 }
 
-// Build the tasks of one instance (one, or several column pieces when its
-// operands do not fit one stage).
-iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int force_variant, uint32_t cap,
+// ------------------------------------------------------ instance pieces
+// An instance whose operands do not fit one pipeline stage, or that exceeds
+// a kernel's tile limits (at most kPieceRows x kPieceCols for the CUDA-core
+// kernel, one 128 x 128 MMA tile for the tensor-core kernel), is cut into
+// pm x pn pieces: its rows into pm near-equal ranges and its columns into pn.
+// Every piece computes its own block of C with the whole K, so the pieces are
+// independent.  K itself is never cut (its pieces would have to accumulate
+// into the same C); an instance whose A and B columns for one output element
+// do not fit a stage is rejected.
+constexpr int kPieceRows = 256, kPieceCols = 256;
+
+void piece_range(int n, int parts, int idx, int &start, int &len)
+{
+    const int base = n / parts, extra = n % parts;
+    start = idx * base + std::min(idx, extra);
+    len = base + (idx < extra ? 1 : 0);
+}
+
+TaskDesc make_piece(const iaat_gemm_desc_t &g, int esz, int Keff, int r0, int h, int c0, int w)
+{
+    TaskDesc d{};
+    d.A = g.A ? static_cast<const char *>(g.A) + (size_t)(g.transA ? (int64_t)r0 * g.lda : (int64_t)r0) * esz
+              : nullptr;
+    d.B = g.B ? static_cast<const char *>(g.B) + (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * esz
+              : nullptr;
+    d.C = static_cast<char *>(g.C) + (size_t)((int64_t)r0 + (int64_t)c0 * g.ldc) * esz;
+    d.lda = g.lda;
+    d.ldb = g.ldb;
+    d.ldc = g.ldc;
+    d.M = (int16_t)h;
+    d.N = (int16_t)w;
+    d.K = (int16_t)Keff;
+    d.ta = (uint8_t)g.transA;
+    d.tb = (uint8_t)g.transB;
+    d.flags = (g.beta != 0.0) ? kFlagReadC : 0;
+    d.alpha = esz == 4 ? (double)(float)g.alpha : g.alpha;
+    d.beta = esz == 4 ? (double)(float)g.beta : g.beta;
+    return d;
+}
+
+bool split_fits(const iaat_gemm_desc_t &g, int esz, int Keff, int pm, int pn, uint32_t cap)
+{
+    for (int i = 0; i < pm; ++i) {
+        int r0, h;
+        piece_range(g.M, pm, i, r0, h);
+        for (int j = 0; j < pn; ++j) {
+            int c0, w;
+            piece_range(g.N, pn, j, c0, w);
+            if (plan_task(make_piece(g, esz, Keff, r0, h, c0, w), esz).total() > cap)
+                return false;
+        }
+    }
+    return true;
+}
+
+// Smallest split (growing the longer side of the pieces first) whose every
+// piece fits `cap` bytes of staging and mcap x ncap elements of C.
+bool choose_split(const iaat_gemm_desc_t &g, int esz, int Keff, uint32_t cap, int mcap, int ncap, int &pm, int &pn)
+{
+    if (Keff > 32767)
+        return false;
+    pm = (g.M + mcap - 1) / mcap;
+    pn = (g.N + ncap - 1) / ncap;
+    for (;;) {
+        if (split_fits(g, esz, Keff, pm, pn, cap))
+            return true;
+        const int h = (g.M + pm - 1) / pm, w = (g.N + pn - 1) / pn;
+        if (h >= w && pm < g.M)
+            ++pm;
+        else if (pn < g.N)
+            ++pn;
+        else if (pm < g.M)
+            ++pm;
+        else
+            return false;
+    }
+}
+
+// Build the tasks of one instance: one, or its pieces.
+iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool tc, int force_variant, uint32_t cap,
                          std::vector<HostTask> &out, int64_t *blocks_out)
 {
     const int M = g.M, N = g.N;
@@ -289,56 +366,28 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, int fo
     const int Keff = (g.alpha == 0.0) ? 0 : g.K;
     if (Keff == 0 && g.beta == 1.0)
         return IAAT_OK;   // C = 1*C: nothing to do
-    for (int pieces = 1; pieces <= N; ++pieces) {
-        const int width = (N + pieces - 1) / pieces;
-        const int np = (N + width - 1) / width;
-        std::vector<HostTask> tmp;
-        bool fits = true;
-        for (int p = 0; p < np && fits; ++p) {
-            const int c0 = p * width;
-            const int nw = std::min(width, N - c0);
-            TaskDesc d{};
-            d.A = static_cast<const char *>(g.A);
-            d.B = g.B ? static_cast<const char *>(g.B) +
-                            (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * esz
-                      : nullptr;
-            d.C = static_cast<char *>(g.C) + (size_t)((int64_t)c0 * g.ldc) * esz;
-            d.lda = g.lda;
-            d.ldb = g.ldb;
-            d.ldc = g.ldc;
-            d.M = (int16_t)M;
-            d.N = (int16_t)nw;
-            d.K = (int16_t)Keff;
-            d.ta = (uint8_t)g.transA;
-            d.tb = (uint8_t)g.transB;
-            d.flags = (g.beta != 0.0) ? kFlagReadC : 0;
-            d.alpha = g.alpha;
-            d.beta = g.beta;
-            if (esz == 4) {
-                d.alpha = (double)(float)g.alpha;
-                d.beta = (double)(float)g.beta;
-            }
-            const TileChoice t = choose_tiling(esz, M, nw, Keff, force_variant);
+    int pm = 1, pn = 1;
+    if (!choose_split(g, esz, Keff, cap, tc ? kTcPackRows : kPieceRows, tc ? kTcPackCols : kPieceCols, pm, pn))
+        return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage (M=%d N=%d K=%d)",
+                    (long long)idx, M, N, g.K);
+    for (int i = 0; i < pm; ++i) {
+        int r0, h;
+        piece_range(M, pm, i, r0, h);
+        for (int j = 0; j < pn; ++j) {
+            int c0, w;
+            piece_range(N, pn, j, c0, w);
+            TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
+            const TileChoice t = choose_tiling(esz, h, w, Keff, force_variant);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
             d.nbn = (uint8_t)t.nbn;
             const TaskStages st = plan_task(d, esz);
-            const uint32_t bytes = st.total();
-            if (bytes > cap) {
-                fits = false;
-                break;
-            }
-            tmp.push_back(HostTask{d, bytes, (double)(st.a.tx + st.b.tx + st.c.tx) + tuning().cost_per_slot * t.cost});
-        }
-        if (fits) {
-            for (auto &t : tmp) {
-                *blocks_out += (int64_t)t.d.nbm * t.d.nbn;
-                out.push_back(t);
-            }
-            return IAAT_OK;
+            *blocks_out += (int64_t)d.nbm * d.nbn;
+            out.push_back(HostTask{d, st.total(),
+                                   (double)(st.a.tx + st.b.tx + st.c.tx) + tuning().cost_per_slot * t.cost});
         }
     }
-    return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage", (long long)idx);
+    return IAAT_OK;
 }
 
 // Order tasks by cost (largest first) and cut them into stages of at most
@@ -368,31 +417,197 @@ void make_groups(std::vector<HostTask> &tasks, uint32_t cap, int max_tasks, std:
 }
 
 // tcgen05 plans: inside each stage, order the tasks by K (largest first) and
-// stack them into packs of at most 128 rows and 128 columns (one MMA tile
-// each).  A task's pack index, row offset and column offset travel in its
-// variant / nbm / nbn fields.  Returns the number of packs.
-int64_t make_packs(std::vector<TaskDesc> &flat, const std::vector<int32_t> &gbeg)
+// place them into packs, one 128-row MMA tile each.  A task takes whole
+// 32-row quarters of the tile (the four tensor-memory lane quarters, each
+// read back by the warps of one SM sub-partition), so its rows start at a
+// multiple of 32 and the epilogue of a pack is spread over all four
+// sub-partitions; its columns start at a multiple of 16 (one tensor-memory
+// load), and a pack holds at most 128 columns.  A task's pack index, first
+// row and first column travel in its variant/nbm/nbn fields.
+// It also writes each pack's summary (PackInfo: the task, by its index in the
+// stage, owning every quarter and every 16-column block, the largest K and
+// the MMA N) and, per stage, the index of its first pack.
+void make_packs(std::vector<TaskDesc> &flat, const std::vector<int32_t> &gbeg, std::vector<PackInfo> &packs,
+                std::vector<int32_t> &pbeg)
 {
-    int64_t npacks = 0;
+    packs.clear();
+    pbeg.clear();
     for (size_t g = 0; g + 1 < gbeg.size(); ++g) {
+        pbeg.push_back((int32_t)packs.size());
         auto b = flat.begin() + gbeg[g], e = flat.begin() + gbeg[g + 1];
         std::stable_sort(b, e, [](const TaskDesc &x, const TaskDesc &y) { return x.K > y.K; });
-        int pack = 0, rows = 0, cols = 0;
+        int quarters = 4, cols = 0;
         for (auto it = b; it != e; ++it) {
-            if (rows > 0 && (rows + it->M > kTcPackRows || cols + it->N > kTcPackCols)) {
-                ++pack;
-                rows = 0;
+            const int q = (it->M + 31) / 32, w = (it->N + 15) & ~15;
+            if (quarters + q > kTcPackRows / 32 || cols + w > kTcPackCols) {
+                PackInfo pi{};
+                for (int k = 0; k < 4; ++k)
+                    pi.qtask[k] = -1;
+                for (int k = 0; k < 8; ++k)
+                    pi.btask[k] = -1;
+                packs.push_back(pi);
+                quarters = 0;
                 cols = 0;
             }
-            it->variant = (uint8_t)pack;
-            it->nbm = (uint8_t)rows;
+            PackInfo &pi = packs.back();
+            const int t = (int)(it - b);
+            it->variant = (uint8_t)(packs.size() - 1 - pbeg.back());
+            it->nbm = (uint8_t)(32 * quarters);
             it->nbn = (uint8_t)cols;
-            rows += it->M;
-            cols += it->N;
+            for (int k = 0; k < q; ++k)
+                pi.qtask[quarters + k] = (int8_t)t;
+            for (int k = 0; k < w / 16; ++k)
+                pi.btask[cols / 16 + k] = (int8_t)t;
+            pi.kmax = (int16_t)std::max<int>(pi.kmax, it->K);
+            quarters += q;
+            cols += w;
+            pi.nt = (uint8_t)std::max(16, cols);
         }
-        npacks += pack + 1;
     }
-    return npacks;
+    pbeg.push_back((int32_t)packs.size());
+}
+
+// Stage programs (see common.cuh): the producer's whole per-stage work,
+// computed once per plan.  The ring placement follows each CTA's sequence of
+// stages: a stage takes the F bytes after the previous one (wrapping to the
+// ring's start when they do not fit), and before writing it must see the
+// release of the latest earlier stage whose bytes it overlaps, or of the
+// previous user of its slot -- releases happen in stage order, so that one
+// wait covers every earlier stage.
+void emit_copies(const Stage &st, const char *p, int h, int w, int ld, int esz, uint32_t dst, uint32_t bar,
+                 std::vector<CopyCmd> &cmds)
+{
+    if (st.bytes == 0)
+        return;
+    const uint64_t pa = (uint64_t)(uintptr_t)p;
+    if (st.span) {
+        cmds.push_back(CopyCmd{reinterpret_cast<const char *>(pa & ~15ull), dst, st.bytes | (bar << 24)});
+        return;
+    }
+    const uint32_t head = (uint32_t)(pa & 15);
+    const uint64_t ldb = (uint64_t)ld * esz;
+    for (int j = 0; j < w; ++j) {
+        const uint64_t c0 = pa + (uint64_t)j * ldb;
+        const uint64_t g0 = c0 & ~15ull, g1 = (c0 + (uint64_t)h * esz + 15) & ~15ull;
+        cmds.push_back(CopyCmd{reinterpret_cast<const char *>(g0), dst + ((head + (uint32_t)j * st.cs) & ~15u),
+                               (uint32_t)(g1 - g0) | (bar << 24)});
+    }
+}
+
+iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vector<int32_t> &gbeg,
+                             const std::vector<PackInfo> &packs, const std::vector<int32_t> &pbeg, int esz, bool tc,
+                             int grid, uint32_t ring_off, uint32_t ring_bytes, std::vector<char> &prog,
+                             std::vector<int64_t> &poff)
+{
+    const int ng = (int)gbeg.size() - 1;
+    poff.assign((size_t)std::max(ng, 1), 0);
+    prog.clear();
+    std::vector<CopyCmd> cmds;
+    std::vector<TaskRec> recs;
+    for (int c = 0; c < grid; ++c) {
+        uint32_t head = 0, rbeg[kNumSlots] = {}, rend[kNumSlots] = {};
+        int oldest = 0;
+        for (int i = 0;; ++i) {
+            const int g = sched_group(i, c, grid);
+            if (g >= ng)
+                break;
+            const int t0 = gbeg[g], nt = gbeg[g + 1] - t0;
+            const int npk = tc ? pbeg[g + 1] - pbeg[g] : 0;
+            if (nt < 0 || nt > kMaxGroupTasks || npk < 0 || npk > kMaxGroupTasks)
+                return fail(IAAT_ERR_INVALID_VALUE, "stage %d has %d tasks", g, nt);
+            TaskStages st[kMaxGroupTasks];
+            uint32_t F = 0;
+            for (int t = 0; t < nt; ++t) {
+                st[t] = plan_task(flat[t0 + t], esz);
+                F += st[t].total();
+            }
+            if (F > ring_bytes)
+                return fail(IAAT_ERR_UNSUPPORTED, "stage %d needs %u bytes of staging", g, F);
+            const uint32_t a = (head + F <= ring_bytes) ? head : 0u;
+            int need = i - kNumSlots;   // the slot's previous user
+            for (int s = i - 1; s >= oldest && s > need; --s) {
+                const int ss = s % kNumSlots;
+                if (F > 0 && rbeg[ss] < a + F && a < rend[ss]) {
+                    need = s;
+                    break;
+                }
+            }
+            int wait = -1;
+            if (need >= oldest) {
+                wait = need;
+                oldest = need + 1;
+            }
+            rbeg[i % kNumSlots] = a;
+            rend[i % kNumSlots] = a + F;
+            head = a + F;
+
+            SlotHeader hd{};
+            hd.ntasks = nt;
+            hd.npacks = npk;
+            uint32_t tx[kMaxGroupTasks] = {};
+            uint32_t ctx = 0, excl = 0;
+            int nbi = 0;
+            cmds.clear();
+            recs.assign((size_t)nt, TaskRec{});
+            for (int t = 0; t < nt; ++t) {
+                const TaskDesc &d = flat[t0 + t];
+                const TaskStages &s = st[t];
+                const uint32_t base = ring_off + a + excl;
+                TaskRec &r = recs[t];
+                r.C = d.C;
+                r.ldc = d.ldc;
+                r.offA = (int32_t)(base + ((uint32_t)(uintptr_t)d.A & 15u));
+                r.offB = (int32_t)(base + s.a.bytes + ((uint32_t)(uintptr_t)d.B & 15u));
+                r.offC = (int32_t)(base + s.a.bytes + s.b.bytes + ((uint32_t)(uintptr_t)d.C & 15u));
+                r.csA = (int32_t)s.a.cs;
+                r.csB = (int32_t)s.b.cs;
+                r.csC = (int32_t)s.c.cs;
+                r.M = d.M; r.N = d.N; r.K = d.K;
+                r.ta = d.ta; r.tb = d.tb; r.variant = d.variant; r.flags = d.flags;
+                r.nbm = d.nbm; r.nbn = d.nbn;
+                r.alpha = d.alpha; r.beta = d.beta;
+                nbi += (int)d.nbm * (int)d.nbn;
+                hd.prefix[t] = nbi;
+                tx[t] = s.a.tx + s.b.tx + (tc ? 0u : s.c.tx);
+                if (tc)
+                    ctx += s.c.tx;
+                int ha, wa, hb, wb;
+                stored_dims(d, ha, wa, hb, wb);
+                const bool prod = d.K > 0;
+                emit_copies(s.a, d.A, prod ? ha : 0, prod ? wa : 0, d.lda, esz, base, (uint32_t)t, cmds);
+                emit_copies(s.b, d.B, prod ? hb : 0, prod ? wb : 0, d.ldb, esz, base + s.a.bytes, (uint32_t)t, cmds);
+                emit_copies(s.c, d.C, d.M, d.N, d.ldc, esz, base + s.a.bytes + s.b.bytes, tc ? kCmdBarC : (uint32_t)t,
+                            cmds);
+                excl += s.total();
+            }
+            for (int t = nt; t < kMaxGroupTasks; ++t)
+                hd.prefix[t] = 0x7fffffff;
+            hd.nblocks = nbi;
+            if (cmds.size() > 0xffff)
+                return fail(IAAT_ERR_UNSUPPORTED, "stage %d needs %zu copies", g, cmds.size());
+
+            StageProg h{};
+            h.wait = wait;
+            h.rec_bytes = (uint32_t)(sizeof(SlotHeader) + nt * sizeof(TaskRec));
+            h.ncmd = (uint16_t)cmds.size();
+            h.nt = (uint8_t)nt;
+            h.npk = (uint8_t)npk;
+            h.ctx = ctx;
+            poff[g] = (int64_t)prog.size();
+            auto put = [&prog](const void *p, size_t n) {
+                const char *c = static_cast<const char *>(p);
+                prog.insert(prog.end(), c, c + n);
+            };
+            put(&h, sizeof h);
+            put(tx, sizeof tx);
+            put(cmds.data(), cmds.size() * sizeof(CopyCmd));
+            put(&hd, sizeof hd);
+            put(recs.data(), recs.size() * sizeof(TaskRec));
+            if (npk > 0)
+                put(&packs[pbeg[g]], (size_t)npk * sizeof(PackInfo));
+        }
+    }
+    return IAAT_OK;
 }
 
 }  // namespace
@@ -453,7 +668,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         if (st != IAAT_OK)
             return st;
         const size_t before = tasks.size();
-        st = make_tasks(i, g, esz, force_variant, cap, tasks, &nblocks);
+        st = make_tasks(i, g, esz, tc, force_variant, cap, tasks, &nblocks);
         if (st != IAAT_OK)
             return st;
         if (tasks.size() > before) {
@@ -465,11 +680,13 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     }
     std::vector<TaskDesc> flat;
     std::vector<int32_t> gbeg;
+    std::vector<PackInfo> packs;
+    std::vector<int32_t> pbeg;
     make_groups(tasks, cap, max_tasks, flat, gbeg);
-    if (tc)
-        nblocks = make_packs(flat, gbeg);
-    if (opts && opts->inject_fault == 1 && gbeg.size() >= 2)
-        gbeg[1] = gbeg[0] + kMaxGroupTasks + 1;   // a stage the kernel must reject
+    if (tc) {
+        make_packs(flat, gbeg, packs, pbeg);
+        nblocks = (int64_t)packs.size();
+    }
 
     iaat_plan_s *plan = new (std::nothrow) iaat_plan_s;
     if (!plan)
@@ -489,29 +706,41 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     plan->precision = precision;
     plan->ntasks = (int64_t)flat.size();
     plan->ngroups = (int64_t)gbeg.size() - 1;
-    const size_t tb = std::max<size_t>(1, flat.size()) * sizeof(TaskDesc);
-    const size_t gb = gbeg.size() * sizeof(int32_t);
-    if ((e = cudaMalloc(&plan->d_tasks, tb)) != cudaSuccess || (e = cudaMalloc(&plan->d_gbeg, gb)) != cudaSuccess ||
+    const int sms = sm_count(plan->device);
+    plan->grid = (int)std::min<int64_t>(plan->ngroups, (int64_t)sms);
+    uint32_t ring_off = 0, ring_size = 0;
+    if (tc)
+        tc_ring((int)precision, &ring_off, &ring_size);
+    else
+        fma_ring(esz, &ring_off, &ring_size);
+    std::vector<char> prog;
+    std::vector<int64_t> poff;
+    iaat_status_t bs = build_programs(flat, gbeg, packs, pbeg, esz, tc, plan->grid, ring_off, ring_size, prog, poff);
+    if (bs != IAAT_OK) {
+        delete plan;
+        return bs;
+    }
+    if (opts && opts->inject_fault == 1 && !prog.empty()) {
+        // the first stage claims more tasks than a stage can hold
+        StageProg *h = reinterpret_cast<StageProg *>(prog.data() + poff[0]);
+        h->nt = (uint8_t)(kMaxGroupTasks + 1);
+    }
+    const size_t pb = std::max<size_t>(16, prog.size()), ob = poff.size() * sizeof(int64_t);
+    if ((e = cudaMalloc(&plan->d_prog, pb)) != cudaSuccess || (e = cudaMalloc(&plan->d_poff, ob)) != cudaSuccess ||
         (e = cudaMalloc(&plan->d_err, sizeof(int32_t))) != cudaSuccess) {
         iaat_plan_destroy(plan);
         return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
     }
-    if (!flat.empty() && (e = cudaMemcpy(plan->d_tasks, flat.data(), flat.size() * sizeof(TaskDesc),
-                                         cudaMemcpyHostToDevice)) != cudaSuccess) {
-        iaat_plan_destroy(plan);
-        return cuda_fail(e, "upload tasks");
-    }
-    if ((e = cudaMemcpy(plan->d_gbeg, gbeg.data(), gb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+    if ((!prog.empty() && (e = cudaMemcpy(plan->d_prog, prog.data(), prog.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(plan->d_poff, poff.data(), ob, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(plan->d_err, 0, sizeof(int32_t))) != cudaSuccess) {
         iaat_plan_destroy(plan);
-        return cuda_fail(e, "upload groups");
+        return cuda_fail(e, "upload the stage programs");
     }
-    const int sms = sm_count(plan->device);
-    plan->grid = (int)std::min<int64_t>(plan->ngroups, (int64_t)sms);
     info.tasks = plan->ntasks;
     info.groups = plan->ngroups;
     info.blocks = nblocks;
-    info.plan_bytes = (int64_t)(tb + gb + sizeof(int32_t));
+    info.plan_bytes = (int64_t)(pb + ob + sizeof(int32_t));
     info.grid = plan->grid;
     info.kernels = plan->ngroups > 0 ? 1 : 0;
     plan->info = info;
@@ -527,8 +756,8 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
         return IAAT_OK;
     KParams kp;
     std::memset(&kp, 0, sizeof kp);
-    kp.p.tasks = plan->d_tasks;
-    kp.p.gbeg = plan->d_gbeg;
+    kp.p.prog = plan->d_prog;
+    kp.p.poff = plan->d_poff;
     kp.p.ngroups = (int32_t)plan->ngroups;
     kp.p.err = plan->d_err;
     cudaError_t e = plan->precision != IAAT_PREC_DEFAULT
@@ -594,10 +823,10 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
     if (cur != plan->device)
         cudaSetDevice(plan->device);
     cudaDeviceSynchronize();
-    if (plan->d_tasks)
-        cudaFree(plan->d_tasks);
-    if (plan->d_gbeg)
-        cudaFree(plan->d_gbeg);
+    if (plan->d_prog)
+        cudaFree(plan->d_prog);
+    if (plan->d_poff)
+        cudaFree(plan->d_poff);
     if (plan->d_err)
         cudaFree(plan->d_err);
     if (cur >= 0 && cur != plan->device)
@@ -617,13 +846,14 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     iaat_gemm_desc_t g{M, N, K, lda, ldb, ldc, ta, tb, alpha, beta, A, B, C};
     std::vector<HostTask> tasks;
     int64_t nb = 0;
-    st = make_tasks(0, g, esz, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks, &nb);
+    st = make_tasks(0, g, esz, false, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks,
+                    &nb);
     if (st != IAAT_OK)
         return st;
     if (tasks.empty())
         return IAAT_OK;
-    if (tasks.size() > (size_t)kInline)
-        return fail(IAAT_ERR_UNSUPPORTED, "instance needs %zu pieces", tasks.size());
+    if (tasks.size() > (size_t)kInline)   // too many pieces for the parameter block
+        return iaat_gemm_grouped_noalloc(&g, 1, esz == 4 ? IAAT_F32 : IAAT_F64, stream);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
@@ -678,7 +908,7 @@ extern "C" iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops)
 // The planning of iaat_plan_create, written into fixed arrays supplied by
 // the caller instead of growing containers, for the entry point that must
 // not allocate (iaat_gemm_grouped_noalloc).  Same validation, tiling,
-// column splitting, ordering and stage cutting as the regular planner.
+// piece splitting, ordering and stage cutting as the regular planner.
 iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, int esz, int max_tasks,
                                  TaskDesc *tasks, uint32_t *bytes, double *cost, int32_t *order, TaskDesc *out,
                                  int32_t *gbeg, int64_t *ntasks_out, int64_t *ngroups_out)
@@ -697,55 +927,32 @@ iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, i
         const int Keff = (g.alpha == 0.0) ? 0 : g.K;
         if (Keff == 0 && g.beta == 1.0)
             continue;
-        bool placed = false;
-        for (int pieces = 1; pieces <= N && !placed; ++pieces) {
-            const int width = (N + pieces - 1) / pieces;
-            const int np = (N + width - 1) / width;
-            if (nt + np > max_tasks)
-                return fail(IAAT_ERR_INVALID_VALUE,
-                            "instance %lld: the batch needs more than %d tasks, the limit of the allocation-free "
-                            "entry point", (long long)i, max_tasks);
-            bool fits = true;
-            for (int p = 0; p < np && fits; ++p) {
-                const int c0 = p * width;
-                const int nw = std::min(width, N - c0);
-                TaskDesc d{};
-                d.A = static_cast<const char *>(g.A);
-                d.B = g.B ? static_cast<const char *>(g.B) +
-                                (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * esz
-                          : nullptr;
-                d.C = static_cast<char *>(g.C) + (size_t)((int64_t)c0 * g.ldc) * esz;
-                d.lda = g.lda;
-                d.ldb = g.ldb;
-                d.ldc = g.ldc;
-                d.M = (int16_t)M;
-                d.N = (int16_t)nw;
-                d.K = (int16_t)Keff;
-                d.ta = (uint8_t)g.transA;
-                d.tb = (uint8_t)g.transB;
-                d.flags = (g.beta != 0.0) ? kFlagReadC : 0;
-                d.alpha = esz == 4 ? (double)(float)g.alpha : g.alpha;
-                d.beta = esz == 4 ? (double)(float)g.beta : g.beta;
-                const TileChoice t = choose_tiling(esz, M, nw, Keff, -1);
+        int pm = 1, pn = 1;
+        if (!choose_split(g, esz, Keff, cap, kPieceRows, kPieceCols, pm, pn))
+            return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage (M=%d N=%d K=%d)",
+                        (long long)i, M, N, g.K);
+        if (nt + (int64_t)pm * pn > max_tasks)
+            return fail(IAAT_ERR_INVALID_VALUE,
+                        "instance %lld: the batch needs more than %d tasks, the limit of the allocation-free "
+                        "entry point", (long long)i, max_tasks);
+        for (int pi = 0; pi < pm; ++pi) {
+            int r0, h;
+            piece_range(M, pm, pi, r0, h);
+            for (int pj = 0; pj < pn; ++pj) {
+                int c0, w;
+                piece_range(N, pn, pj, c0, w);
+                TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
+                const TileChoice t = choose_tiling(esz, h, w, Keff, -1);
                 d.variant = (uint8_t)t.variant;
                 d.nbm = (uint8_t)t.nbm;
                 d.nbn = (uint8_t)t.nbn;
                 const TaskStages sg = plan_task(d, esz);
-                if (sg.total() > cap) {
-                    fits = false;
-                    break;
-                }
-                tasks[nt + p] = d;
-                bytes[nt + p] = sg.total();
-                cost[nt + p] = (double)(sg.a.tx + sg.b.tx + sg.c.tx) + tuning().cost_per_slot * t.cost;
-            }
-            if (fits) {
-                nt += np;
-                placed = true;
+                tasks[nt] = d;
+                bytes[nt] = sg.total();
+                cost[nt] = (double)(sg.a.tx + sg.b.tx + sg.c.tx) + tuning().cost_per_slot * t.cost;
+                ++nt;
             }
         }
-        if (!placed)
-            return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage", (long long)i);
     }
     // largest cost first, ties in input order (the regular planner's stable order)
     for (int64_t k = 0; k < nt; ++k)

@@ -30,6 +30,12 @@ cudaError_t launch_fma(int dtype, const KParams &kp, int grid, cudaStream_t stre
     return cudaGetLastError();
 }
 
+void fma_ring(int esz, uint32_t *off, uint32_t *bytes)
+{
+    *off = esz == 4 ? smem_ring_offset<4>() : smem_ring_offset<8>();
+    *bytes = esz == 4 ? ring_bytes<4>() : ring_bytes<8>();
+}
+
 cudaError_t single_call_err_ptr(int32_t **p)
 {
     return cudaGetSymbolAddress(reinterpret_cast<void **>(p), g_single_call_err);

@@ -53,4 +53,19 @@ int tc_group_cap(int precision)
     }
 }
 
+void tc_ring(int precision, uint32_t *off, uint32_t *bytes)
+{
+    switch (precision) {
+    case kTc3xBF16:
+        *off = tc_ring_offset<kTc3xBF16>(), *bytes = tc_ring_bytes<kTc3xBF16>();
+        break;
+    case kTcTF32:
+        *off = tc_ring_offset<kTcTF32>(), *bytes = tc_ring_bytes<kTcTF32>();
+        break;
+    default:
+        *off = tc_ring_offset<kTcFP16>(), *bytes = tc_ring_bytes<kTcFP16>();
+        break;
+    }
+}
+
 }  // namespace iaat

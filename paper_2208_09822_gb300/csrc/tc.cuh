@@ -2,32 +2,35 @@
 // and out: 3xBF16 split products, TF32, or FP16 inputs, FP32 accumulation in
 // tensor memory.
 //
-// Packs: the planner stacks the tasks of a stage into packs of at most 128
-// rows and 128 columns; task t owns rows R_t.. of the MMA tile and columns
-// C_t.. of the concatenated B, so several small instances share one
-// tensor-core pass and only the diagonal blocks of the product are kept
-// (the pack index, R_t and C_t travel in the task's variant/nbm/nbn fields).
+// Packs: the planner places the tasks of a stage into packs, one 128-row MMA
+// tile each.  A task owns whole 32-row quarters of the tile (its rows start
+// at R_t, a multiple of 32) and a run of 16-column blocks (its columns start
+// at C_t, a multiple of 16), so several small instances share one
+// tensor-core pass and only the diagonal blocks of the product are kept.
+// The quarters matter because tensor-memory lanes 32q..32q+31 can only be
+// read by the warps of SM sub-partition q: one task per quarter spreads each
+// pack's epilogue over all four sub-partitions.
 //
 // Warp roles (18 warps):
 //   0-7  converters: per 32-wide K-chunk of a pack, every thread converts one
-//        row of the 128-row tile -- warps 0-3 the rows of op(A), warps 4-7
-//        the rows of op(B)^T -- from the staged FP32 data into the canonical
-//        K-major (no swizzle) operand layout of one of two operand stages:
-//        X = Xh + Xl (BF16) for 3xBF16, RN-rounded TF32, or FP16, with zeros
-//        past the row's K;
-//   8-15 epilogue: when a pack's accumulator is complete, read each row of
-//        it from tensor memory (warps 8+q and 12+q own lanes 32q..32q+31 and
-//        take alternate 16-column chunks) and write alpha*acc + beta*C0 to
-//        exactly the task's elements;
+//        row of a 128-row operand tile -- warps 0-3 the rows of op(A) (one
+//        quarter each), warps 4-7 the rows of op(B)^T -- from the staged FP32
+//        data into the canonical K-major (no swizzle) layout of one of
+//        kTcStages operand stages: X = Xh + Xl (BF16) for 3xBF16,
+//        RN-rounded TF32, or FP16, with zeros past the row's K;
+//   8-15 epilogue: warp 8+e reads quarter e&3 of the accumulator of every
+//        pack whose sequence number has parity e>>2, batching two 16-column
+//        tensor-memory loads per wait, and writes alpha*acc +
+//        beta*C0 to exactly the task's elements;
 //   16   producer: streams stages into the shared-memory ring (shared with
-//        the CUDA-core kernel);
-//   17   MMA: one lane issues the chunk's MMAs into one of two accumulators
-//        and commits them to mbarriers that free the operand stage and, after
-//        a pack's last chunk, hand the accumulator to the epilogue.
-// Conversion of chunk c+1, the MMAs of chunk c and the epilogue of the
-// previous pack run at the same time.  Every wait is bounded; a time-out sets
-// the error word, every role leaves its loop, and the CTA frees its tensor
-// memory before returning.
+//        the CUDA-core kernel) and summarises each pack (PackInfo);
+//   17   MMA: one lane issues each chunk's MMAs into one of kTcAccs
+//        accumulators and commits them to mbarriers that free the operand
+//        stage and, after a pack's last chunk, hand the accumulator over.
+// Conversion of the next chunks, the MMAs of this one and the epilogue of up
+// to kTcAccs - 1 earlier packs run at the same time.  Every wait is bounded;
+// a time-out sets the error word, every role leaves its loop, and the CTA
+// frees its tensor memory before returning.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -37,14 +40,15 @@
 namespace iaat {
 
 constexpr int kTc3xBF16 = 1, kTcTF32 = 2, kTcFP16 = 3;
-constexpr int kTcRows = 128;           // MMA M (TMEM lanes)
+constexpr int kTcRows = 128;           // MMA M (tensor-memory lanes)
 constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
 constexpr int kTcKC = 32;              // K per operand stage
 constexpr int kTcStages = 2;           // operand stages
+constexpr int kTcAccs = 4;             // accumulators of kTcMaxCols columns
 constexpr int kTcConvWarps = 8, kTcEpiWarps = 8;
 constexpr int kTcWarpProducer = 16, kTcWarpMma = 17;
 constexpr int kTcThreads = 576;
-constexpr int kTcTmemCols = 256;       // two accumulators of 128 columns
+constexpr int kTcTmemCols = kTcAccs * kTcMaxCols;
 
 template <int P> struct TcTraits;
 template <> struct TcTraits<kTc3xBF16> {
@@ -68,19 +72,25 @@ template <int P> IAAT_CE int tc_operand_bytes() { return (kTcRows / 8) * tc_sbo<
 template <int P> IAAT_CE int tc_stage_bytes() { return 2 * TcTraits<P>::kTerms * tc_operand_bytes<P>(); }
 
 // shared-memory map (bytes): the ring's barriers and stage records as in the
-// CUDA-core kernel, then this kernel's own barriers, then the operand stages
+// CUDA-core kernel, then this kernel's own barriers and pack summaries, then
+// the operand stages
 constexpr int kTcExtra = kSmemSlots + kNumSlots * kSlotBytes;
-constexpr int kTcBarOpFull = kTcExtra;          // [2], 4 converter-warp arrivals
-constexpr int kTcBarOpEmpty = kTcExtra + 16;    // [2], tcgen05.commit
-constexpr int kTcBarAccFull = kTcExtra + 32;    // [2], tcgen05.commit
-constexpr int kTcBarAccEmpty = kTcExtra + 48;   // [2], 4 epilogue-warp arrivals
-constexpr int kTcTmemSlot = kTcExtra + 64;      // tcgen05.alloc result
-constexpr int kTcChunkInfo = kTcExtra + 80;     // [2] x 16 B
-constexpr int kTcOperands = (kTcExtra + 128 + 1023) & ~1023;
+constexpr int kTcBarOpFull = kTcExtra;          // [kTcStages], kTcConvWarps arrivals
+constexpr int kTcBarOpEmpty = kTcExtra + 32;    // [kTcStages], tcgen05.commit
+constexpr int kTcBarAccFull = kTcExtra + 64;    // [kTcAccs], tcgen05.commit
+constexpr int kTcBarAccEmpty = kTcExtra + 96;   // [kTcAccs], 4 epilogue-warp arrivals
+constexpr int kTcBarCFull = kTcExtra + 128;     // [kNumSlots], the stage's C copies
+constexpr int kTcTmemSlot = kTcExtra + 192;     // tcgen05.alloc result
+constexpr int kTcChunkInfo = kTcExtra + 256;    // [kTcStages] x 16 B
+constexpr int kTcPackInfo = kTcExtra + 320;     // PackInfo[kNumSlots][kMaxGroupTasks]
+constexpr int kTcOperands = (kTcPackInfo + kNumSlots * kMaxGroupTasks * (int)sizeof(PackInfo) + 1023) & ~1023;
 static_assert(kTcExtra % 16 == 0, "barrier alignment");
+static_assert(kTcStages <= 4 && kTcAccs <= 4 && kNumSlots <= 8, "barrier space");
+static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps == 8, "accumulator rotation");
 template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + kTcStages * tc_stage_bytes<P>(); }
 template <int P> IAAT_CE int tc_ring_bytes() { return (kSmemTotal - tc_ring_offset<P>()) & ~127; }
-template <int P> IAAT_CE int tc_max_group_bytes() { return tc_ring_bytes<P>() / 2; }
+// A stage may take at most a third of the ring, so three are in flight.
+template <int P> IAAT_CE int tc_max_group_bytes() { return tc_ring_bytes<P>() / 3; }
 
 struct ChunkInfo {      // converters -> MMA warp, one per operand stage
     int32_t nt;         // MMA N of the pack
@@ -150,18 +160,33 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// 16 consecutive accumulator columns of this warp's 32 tensor-memory lanes
+// into r[OFF..OFF+15] (thread t gets lane 32q + t); completes at tmem_wait_ld.
+template <int OFF>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=r"(r[OFF + 0]), "=r"(r[OFF + 1]), "=r"(r[OFF + 2]), "=r"(r[OFF + 3]), "=r"(r[OFF + 4]),
+          "=r"(r[OFF + 5]), "=r"(r[OFF + 6]), "=r"(r[OFF + 7]), "=r"(r[OFF + 8]), "=r"(r[OFF + 9]),
+          "=r"(r[OFF + 10]), "=r"(r[OFF + 11]), "=r"(r[OFF + 12]), "=r"(r[OFF + 13]), "=r"(r[OFF + 14]),
+          "=r"(r[OFF + 15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        v[i] = __uint_as_float(r[i]);
+}
+
+// Wait for this thread's outstanding tensor-memory loads.  The destination
+// registers pass through the statement so that no use of them can be
+// scheduled ahead of the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
+                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 // ------------------------------------------------------- conversions
@@ -215,54 +240,6 @@ __device__ __forceinline__ void store_row(char *t0, char *t1, uint32_t off, cons
     }
 }
 
-// Convert one task operand's K-chunk [k0, k0 + kc) into canonical rows
-// [row0, row0 + rows) of an operand stage.  raw(i, k) = src + i*si + k*sk.
-// Values with k >= K are zero.  kcontig: the staged data is contiguous along
-// k, so a lane takes one core-matrix row (lanes: rows x K-groups); otherwise
-// it is contiguous along the rows and lanes run along the rows.
-template <int P>
-__device__ __forceinline__ void convert_chunk(char *t0, char *t1, const char *src, int si, int sk, int rows, int K,
-                                              int row0, int k0, int kc, bool kcontig)
-{
-    constexpr int VPR = tc_vpr<P>();
-    constexpr int KGM = tc_kgroups<P>();
-    constexpr int SBO = tc_sbo<P>();
-    const int lane = (int)lane_id();
-    const int ng = kc / VPR;
-    if (kcontig) {
-        constexpr int RPS = 32 / KGM;            // rows per warp step
-        const int g = lane % KGM, rr = lane / KGM;
-        if (g < ng) {
-            const int kb = k0 + g * VPR;
-#pragma unroll 1
-            for (int r = rr; r < rows; r += RPS) {
-                const char *p = src + r * si + kb * sk;
-                float x[8];
-#pragma unroll
-                for (int e = 0; e < VPR; ++e)
-                    x[e] = (kb + e < K) ? *reinterpret_cast<const float *>(p + e * sk) : 0.0f;
-                const int row = row0 + r;
-                store_row<P>(t0, t1, (uint32_t)((row >> 3) * SBO + g * 128 + (row & 7) * 16), x);
-            }
-        }
-    } else {
-#pragma unroll 1
-        for (int r = lane; r < rows; r += 32) {
-            const int row = row0 + r;
-            const char *p = src + r * si;
-#pragma unroll 1
-            for (int g = 0; g < ng; ++g) {
-                const int kb = k0 + g * VPR;
-                float x[8];
-#pragma unroll
-                for (int e = 0; e < VPR; ++e)
-                    x[e] = (kb + e < K) ? *reinterpret_cast<const float *>(p + (kb + e) * sk) : 0.0f;
-                store_row<P>(t0, t1, (uint32_t)((row >> 3) * SBO + g * 128 + (row & 7) * 16), x);
-            }
-        }
-    }
-}
-
 struct TcSmem {
     SmemMap S;
     __device__ uint32_t op_full(int b) const { return S.sbase + kTcBarOpFull + 8 * b; }
@@ -272,60 +249,14 @@ struct TcSmem {
     __device__ ChunkInfo *info(int b) const { return reinterpret_cast<ChunkInfo *>(S.base + kTcChunkInfo) + b; }
 };
 
-// Per-warp view of a stage's tasks: lane t holds task t's fields.
-struct LaneTask {
-    int M, N, K, R, Cc, pack, ta, tb, offA, offB, csA, csB;
-};
-
-__device__ __forceinline__ LaneTask load_lane_task(const TaskRec *recs, int nt)
-{
-    const int lane = (int)lane_id();
-    LaneTask me{0, 0, 0, 0, 0, 1 << 20, 0, 0, 0, 0, 0, 0};
-    if (lane < nt) {
-        const TaskRec &r = recs[lane];
-        me = LaneTask{r.M, r.N, r.K, r.nbm, r.nbn, r.variant, r.ta, r.tb, r.offA, r.offB, r.csA, r.csB};
-    }
-    return me;
-}
-
-__device__ __forceinline__ int warp_max(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Pack p's task mask, K (rounded to the MMA K step) and MMA N.
-template <int P>
-__device__ __forceinline__ void pack_shape(const LaneTask &me, int nt, int p, unsigned &mask, int &KT, int &NT)
-{
-    constexpr int KS = TcTraits<P>::kKStep;
-    const int lane = (int)lane_id();
-    const bool in = lane < nt && me.pack == p;
-    mask = __ballot_sync(0xffffffffu, in);
-    const int kmax = warp_max(in ? me.K : 0);
-    const int cmax = warp_max(in ? me.Cc + me.N : 0);
-    KT = (kmax + KS - 1) / KS * KS;
-    NT = max(16, (cmax + 15) & ~15);
-}
-
 // Bounded wait on an mbarrier phase by every lane of a warp.  Each lane
 // performs the acquire itself, so each lane's later reads of what was
-// published with the barrier (stage records, chunk records, operand data)
-// see the new values; lanes that only learned of the phase from another lane
-// could read stale records, take different branches and deadlock the warp at
-// its next collective.  The outcome is made warp-uniform.
+// published with the barrier (stage records, pack summaries, staged data)
+// see the new values.  The outcome is made warp-uniform.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
 {
-    // lane 0 does the (suspending) wait; then every lane confirms the
-    // completed phase with its own try_wait, which is its acquire
-    int ok = 1;
-    if (lane_id() == 0)
-        ok = mbar_wait(bar, parity, kWaitLimitNs) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    const bool mine = ok && mbar_wait(bar, parity, kWaitLimitNs);
-    return __all_sync(0xffffffffu, mine);
+    const bool ok = mbar_wait(bar, parity, kWaitLimitNs);
+    return __all_sync(0xffffffffu, ok);
 }
 
 template <int P>
@@ -335,8 +266,10 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
     const int lane = (int)lane_id();
     constexpr int OPB = tc_operand_bytes<P>();
     constexpr int VPR = tc_vpr<P>();
-    const int side = cw >> 2;                 // 0: A rows, 1: B rows
-    const int row = 32 * (cw & 3) + lane;     // this thread's pack row
+    constexpr int KS = TcTraits<P>::kKStep;
+    const int side = cw >> 2;                 // 0: rows of op(A), 1: rows of op(B)^T
+    const int row = 32 * (cw & 3) + lane;     // this thread's row of the operand tile
+    const uint32_t row_off = (uint32_t)((row >> 3) * tc_sbo<P>() + (row & 7) * 16);
     int b = 0;
     uint32_t bpar = 0;     // parity of the operand stages' current round
     int uses = 0;          // chunks handed to the MMA warp so far
@@ -346,49 +279,42 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
         if (g >= Pm.ngroups)
             break;
         const int slot = i % kNumSlots;
-        if (!warp_wait(T.S.full(slot), (uint32_t)((i / kNumSlots) & 1))) {
+        const uint32_t par = (uint32_t)((i / kNumSlots) & 1);
+        if (!warp_wait(T.S.full(slot), par)) {
             if (lane == 0)
                 set_error(Pm.err, kErrTimeoutFull);
             alive = false;
             break;
         }
         const TaskRec *recs = T.S.recs(slot);
-        const int nt = T.S.header(slot)->ntasks;
-        const LaneTask me = load_lane_task(recs, nt);
-        const int npacks = warp_max(lane < nt ? me.pack + 1 : 0);
-        for (int p = 0; p < npacks && alive; ++p) {
-            unsigned mask;
-            int KT, NT;
-            pack_shape<P>(me, nt, p, mask, KT, NT);
+        const PackInfo *pis = T.S.pinfo(slot);
+        const int npk = T.S.header(slot)->npacks;
+        for (int p = 0; p < npk && alive; ++p) {
+            const PackInfo &pi = pis[p];
+            const int t = side == 0 ? pi.qtask[cw & 3] : pi.btask[row >> 4];
+            const int KT = ((int)pi.kmax + KS - 1) / KS * KS;
+            const int NT = pi.nt;
             const int nch = KT > 0 ? (KT + kTcKC - 1) / kTcKC : 1;
-            // the task owning this thread's row of the pack (A rows for warps
-            // 0-3, B rows for warps 4-7), and where that row's data sits
-            int my_task = -1;
-            for (unsigned m = mask; m; m &= m - 1) {
-                const int c = __ffs(m) - 1;
-                const int lo = __shfl_sync(0xffffffffu, side == 0 ? me.R : me.Cc, c);
-                const int len = __shfl_sync(0xffffffffu, side == 0 ? me.M : me.N, c);
-                if (row >= lo && row < lo + len)
-                    my_task = c;
+            // this thread's row: row r of task t's op(A), or column r of its op(B)
+            bool valid = false;
+            int myK = 0, sk = 4;
+            const char *src = T.S.base;
+            if (t >= 0) {
+                const TaskRec &rc = recs[t];
+                const int r = row - (side == 0 ? (int)rc.nbm : (int)rc.nbn);
+                valid = r < (side == 0 ? (int)rc.M : (int)rc.N);
+                // A row i: stored A[i + k*lda] (N) or A[k + i*lda] (T);
+                // B row n (column n of op(B)): stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
+                const int tr = side == 0 ? rc.ta : rc.tb;
+                const bool kcontig = side == 0 ? tr != 0 : tr == 0;
+                const int cs = side == 0 ? rc.csA : rc.csB;
+                sk = kcontig ? 4 : cs;
+                src += (side == 0 ? rc.offA : rc.offB) + r * (kcontig ? cs : 4);
+                myK = rc.K;
             }
-            const int src_lane = my_task >= 0 ? my_task : 0;
-            const int t_lo = __shfl_sync(0xffffffffu, side == 0 ? me.R : me.Cc, src_lane);
-            const int my_K = __shfl_sync(0xffffffffu, me.K, src_lane);
-            const int t_tr = __shfl_sync(0xffffffffu, side == 0 ? me.ta : me.tb, src_lane);
-            const int t_off = __shfl_sync(0xffffffffu, side == 0 ? me.offA : me.offB, src_lane);
-            const int t_cs = __shfl_sync(0xffffffffu, side == 0 ? me.csA : me.csB, src_lane);
-            // A row i: stored A[i + k*lda] (N) or A[k + i*lda] (T);
-            // B row n (column n of op(B)): stored B[k + n*ldb] (N) or B[n + k*ldb] (T)
-            const bool kcontig = side == 0 ? t_tr != 0 : t_tr == 0;
-            const int my_si = kcontig ? t_cs : 4;
-            const int my_sk = kcontig ? 4 : t_cs;
-            const char *my_src = T.S.base + t_off + (row - t_lo) * my_si;
-            const uint32_t row_off = (uint32_t)((row >> 3) * tc_sbo<P>() + (row & 7) * 16);
-            // this row's operand bytes must have landed (each thread acquires
-            // the barrier of its own task)
+            // the operand bytes of this thread's task must have landed
             {
-                const bool ok = my_task < 0 || mbar_wait(T.S.task(slot, my_task),
-                                                         (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs);
+                const bool ok = !valid || mbar_wait(T.S.task(slot, t), par, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0)
                         set_error(Pm.err, kErrTimeoutFull);
@@ -397,36 +323,39 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
                 }
             }
             for (int c = 0; c < nch; ++c) {
-                // the MMAs that read this stage one round ago must be done
-                if (uses >= kTcStages && !warp_wait(T.op_empty(b), bpar ^ 1u)) {
+                if (uses >= kTcStages) {
+                    // the MMAs that read this stage one round ago are complete
+                    int ok = 1;
                     if (lane == 0)
-                        set_error(Pm.err, kErrTimeoutEmpty);
-                    alive = false;
-                    break;
+                        ok = mbar_wait(T.op_empty(b), bpar ^ 1u, kWaitLimitNs) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    __syncwarp();
+                    if (!ok) {
+                        if (lane == 0)
+                            set_error(Pm.err, kErrTimeoutEmpty);
+                        alive = false;
+                        break;
+                    }
                 }
                 const int k0 = c * kTcKC;
                 const int kc = KT > 0 ? min(kTcKC, KT - k0) : 0;
-                char *base = T.S.base + kTcOperands + b * tc_stage_bytes<P>();
-                char *A0 = base, *A1 = base + OPB;
-                char *B0 = base + TcTraits<P>::kTerms * OPB, *B1 = B0 + OPB;
-                if (kc > 0 && my_task >= 0) {
-                    // this thread's pack row: its K-groups of the chunk
-                    char *t0 = side == 0 ? A0 : B0;
-                    char *t1 = side == 0 ? A1 : B1;
+                char *t0 = T.S.base + kTcOperands + b * tc_stage_bytes<P>() + side * TcTraits<P>::kTerms * OPB;
+                char *t1 = t0 + OPB;
+                if (valid && kc > 0) {
                     const int ng = kc / VPR;
 #pragma unroll 1
                     for (int gi = 0; gi < ng; ++gi) {
                         const int kb = k0 + gi * VPR;
-                        const char *p = my_src + kb * my_sk;
+                        const char *q = src + kb * sk;
                         float x[8];
-                        if (kb + VPR <= my_K) {
+                        if (kb + VPR <= myK) {
 #pragma unroll
                             for (int e = 0; e < VPR; ++e)
-                                x[e] = *reinterpret_cast<const float *>(p + e * my_sk);
+                                x[e] = *reinterpret_cast<const float *>(q + e * sk);
                         } else {
 #pragma unroll
                             for (int e = 0; e < VPR; ++e)
-                                x[e] = (kb + e < my_K) ? *reinterpret_cast<const float *>(p + e * my_sk) : 0.0f;
+                                x[e] = (kb + e < myK) ? *reinterpret_cast<const float *>(q + e * sk) : 0.0f;
                         }
                         store_row<P>(t0, t1, row_off + (uint32_t)(gi * 128), x);
                     }
@@ -453,97 +382,93 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
             mbar_arrive(T.S.empty(slot));
     }
     // end-of-work marker for the MMA warp
-    if (alive && (uses < kTcStages || warp_wait(T.op_empty(b), bpar ^ 1u))) {
-        if (cw == 0 && lane == 0) {
-            ChunkInfo *ci = T.info(b);
-            ci->nt = 16;
-            ci->kc = 0;
-            ci->flags = kChunkEnd;
-        }
+    if (alive) {
+        int ok = 1;
+        if (uses >= kTcStages && lane == 0)
+            ok = mbar_wait(T.op_empty(b), bpar ^ 1u, kWaitLimitNs) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
         __syncwarp();
-        if (lane == 0)
-            mbar_arrive(T.op_full(b));
+        if (ok) {
+            if (cw == 0 && lane == 0) {
+                ChunkInfo *ci = T.info(b);
+                ci->nt = 16;
+                ci->kc = 0;
+                ci->flags = kChunkEnd;
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(T.op_full(b));
+        }
     }
 }
 
+// The MMA role: run by one thread.
 template <int P>
-__device__ void tc_mma_warp(const KParams &KP, const TcSmem &T, uint32_t tmem)
+__device__ void tc_mma_thread(const KParams &KP, const TcSmem &T, uint32_t tmem)
 {
     const Params &Pm = KP.p;
-    const int lane = (int)lane_id();
     constexpr int KS = TcTraits<P>::kKStep;
     constexpr int OPB = tc_operand_bytes<P>();
     constexpr uint32_t SBO = (uint32_t)tc_sbo<P>();
-    int b = 0, a = 0;
+    int b = 0;
     uint32_t bpar = 0;
-    uint32_t apar[2] = {0u, 0u};
-    int acc_uses[2] = {0, 0};
-    int commits[kTcStages] = {0, 0};   // tcgen05.commit arrivals sent to op_empty[b]
+    uint32_t pk = 0;     // packs completed
+    int total = 0;       // chunks consumed (each sends one commit to its stage's op_empty)
     for (;;) {
-        if (!warp_wait(T.op_full(b), bpar)) {
-            if (lane == 0)
-                set_error(Pm.err, kErrTimeoutFull);
+        if (!mbar_wait(T.op_full(b), bpar, kWaitLimitNs)) {
+            set_error(Pm.err, kErrTimeoutFull);
             break;
         }
         const ChunkInfo ci = *T.info(b);
         if (ci.flags & kChunkEnd)
             break;
-        if ((ci.flags & kChunkFirst) && acc_uses[a] > 0) {
-            // the epilogue must have drained this accumulator
-            if (!warp_wait(T.acc_empty(a), apar[a] ^ 1u)) {
-                if (lane == 0)
-                    set_error(Pm.err, kErrTimeoutEmpty);
-                break;
-            }
+        const int a = (int)(pk & (kTcAccs - 1));
+        // before a pack's first chunk: the epilogue has drained this accumulator's previous use
+        if ((ci.flags & kChunkFirst) && pk >= (uint32_t)kTcAccs &&
+            !mbar_wait(T.acc_empty(a), ((pk / kTcAccs) - 1u) & 1u, kWaitLimitNs)) {
+            set_error(Pm.err, kErrTimeoutEmpty);
+            break;
         }
-        if (lane == 0) {
-            tc_fence_after();
-            if (ci.kc > 0) {
-                const uint32_t d = tmem + (uint32_t)(a * kTcMaxCols);
-                const uint32_t idesc = tc_idesc<P>(ci.nt);
-                const uint32_t base = smem_addr(T.S.base + kTcOperands + b * tc_stage_bytes<P>());
-                const uint32_t a0 = base, a1 = base + OPB;
-                const uint32_t b0 = base + TcTraits<P>::kTerms * OPB, b1 = b0 + OPB;
-                const bool first = (ci.flags & kChunkFirst) != 0;
-                for (int ks = 0; ks < ci.kc / KS; ++ks) {
-                    const uint32_t o = (uint32_t)ks * 256u;   // two core matrices along K
-                    const uint32_t accum = (first && ks == 0) ? 0u : 1u;
-                    if constexpr (P == kTc3xBF16) {
-                        tc_mma<P>(d, smem_desc(a1 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
-                        tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b1 + o, 128, SBO), idesc, 1);
-                        tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, 1);
-                    } else {
-                        tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
-                    }
+        tc_fence_after();
+        if (ci.kc > 0) {
+            const uint32_t d = tmem + (uint32_t)(a * kTcMaxCols);
+            const uint32_t idesc = tc_idesc<P>(ci.nt);
+            const uint32_t base = smem_addr(T.S.base + kTcOperands + b * tc_stage_bytes<P>());
+            const uint32_t a0 = base, a1 = base + OPB;
+            const uint32_t b0 = base + TcTraits<P>::kTerms * OPB, b1 = b0 + OPB;
+            const bool first = (ci.flags & kChunkFirst) != 0;
+            for (int ks = 0; ks < ci.kc / KS; ++ks) {
+                const uint32_t o = (uint32_t)ks * 256u;   // two core matrices along K
+                const uint32_t accum = (first && ks == 0) ? 0u : 1u;
+                if constexpr (P == kTc3xBF16) {
+                    tc_mma<P>(d, smem_desc(a1 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
+                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b1 + o, 128, SBO), idesc, 1);
+                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, 1);
+                } else {
+                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
                 }
             }
-            tc_commit(T.op_empty(b));
-            if (ci.flags & kChunkLast)
-                tc_commit(T.acc_full(a));
         }
-        __syncwarp();
-        ++commits[b];
+        tc_commit(T.op_empty(b));
         if (ci.flags & kChunkLast) {
-            ++acc_uses[a];
-            apar[a] ^= 1u;
-            a ^= 1;
+            tc_commit(T.acc_full(a));
+            ++pk;
         }
+        ++total;
         if (++b == kTcStages) {
             b = 0;
             bpar ^= 1u;
         }
     }
     // No asynchronous arrival may reach this CTA's shared memory after it
-    // exits: wait (bounded) for the last commit to each operand-stage barrier,
-    // which no other role waits for.  (The accumulator commits are all
-    // waited for by the epilogue.)
-    if (lane == 0) {
-        for (int bb = 0; bb < kTcStages; ++bb)
-            if (commits[bb] > 0 &&
-                !mbar_wait(T.op_empty(bb), (uint32_t)((commits[bb] - 1) & 1), kWaitLimitNs))
-                set_error(Pm.err, kErrTimeoutFull);
+    // exits: wait (bounded) for the last commit to each operand stage, which
+    // no other role is left to wait for.  (The epilogue waits for every
+    // accumulator commit.)
+    for (int bb = 0; bb < kTcStages; ++bb) {
+        const int n = total / kTcStages + (bb < total % kTcStages ? 1 : 0);
+        if (n > 0 && !mbar_wait(T.op_empty(bb), (uint32_t)((n - 1) & 1), kWaitLimitNs))
+            set_error(Pm.err, kErrTimeoutFull);
     }
-    __syncwarp();
 }
 
 template <int P>
@@ -551,80 +476,75 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
 {
     const Params &Pm = KP.p;
     const int lane = (int)lane_id();
-    const int q = ew & 3;                           // TMEM lane quarter (warp index mod 4)
-    const int half = ew >> 2;                       // which alternate 16-column chunks
-    const int row = 32 * q + lane;                  // accumulator row (TMEM lane) of this thread
+    const int q = ew & 3;                           // tensor-memory lane quarter (= warp index mod 4)
+    const int half = ew >> 2;                       // packs of this sequence parity
+    const int row = 32 * q + lane;                  // accumulator row (tensor-memory lane) of this thread
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    int a = 0;
-    uint32_t apar[2] = {0u, 0u};
+    uint32_t pk = 0;                                // pack sequence number
     for (int i = 0;; ++i) {
         const int g = sched_group(i, blockIdx.x, gridDim.x);
         if (g >= Pm.ngroups)
             break;
         const int slot = i % kNumSlots;
-        if (!warp_wait(T.S.full(slot), (uint32_t)((i / kNumSlots) & 1))) {
+        const uint32_t par = (uint32_t)((i / kNumSlots) & 1);
+        if (!warp_wait(T.S.full(slot), par) || !warp_wait(T.S.cfull(slot), par)) {
             if (lane == 0)
                 set_error(Pm.err, kErrTimeoutFull);
             return;
         }
         const TaskRec *recs = T.S.recs(slot);
-        const int nt = T.S.header(slot)->ntasks;
-        const LaneTask me = load_lane_task(recs, nt);
-        const int npacks = warp_max(lane < nt ? me.pack + 1 : 0);
-        for (int p = 0; p < npacks; ++p) {
-            unsigned mask;
-            int KT, NT;
-            pack_shape<P>(me, nt, p, mask, KT, NT);
-            if (!warp_wait(T.acc_full(a), apar[a])) {
+        const PackInfo *pis = T.S.pinfo(slot);
+        const int npk = T.S.header(slot)->npacks;
+        for (int p = 0; p < npk; ++p, ++pk) {
+            if ((int)(pk & 1u) != half)
+                continue;
+            const int a = (int)(pk & (kTcAccs - 1));
+            if (!warp_wait(T.acc_full(a), (pk / kTcAccs) & 1u)) {
                 if (lane == 0)
                     set_error(Pm.err, kErrTimeoutFull);
                 return;
             }
-            apar[a] ^= 1u;
             tc_fence_after();
-            const uint32_t dt = tmem + (uint32_t)(a * kTcMaxCols) + lane_base;
-            // tasks whose rows meet this warp's 32 rows
-            const unsigned rows_mask = __ballot_sync(
-                0xffffffffu, ((mask >> lane) & 1) && me.R < 32 * q + 32 && me.R + me.M > 32 * q);
-            for (unsigned m = rows_mask; m; m &= m - 1) {
-                const int t = __ffs(m) - 1;
-                const TaskRec &r = recs[t];
-                const int R = r.nbm, M = r.M, Cc = r.nbn, N = r.N;
-                const bool mine = row >= R && row < R + M;
-                if (mine && (r.flags & kFlagReadC) &&
-                    !mbar_wait(T.S.task(slot, t), (uint32_t)((i / kNumSlots) & 1), kWaitLimitNs))
-                    set_error(Pm.err, kErrTimeoutFull);
-                const int i_ = mine ? row - R : 0;
-                const float alpha = (float)r.alpha, beta = (float)r.beta;
-                const bool readc = (r.flags & kFlagReadC) != 0;
-                float *C = reinterpret_cast<float *>(r.C) + i_;
-                const int64_t ldc = r.ldc;
-                const char *c0 = T.S.base + r.offC + i_ * 4;
-                const int csC = r.csC;
-                for (int j0 = (Cc & ~15) + 16 * half; j0 < Cc + N; j0 += 32) {
-                    float v[16];
-                    if (KT > 0) {
-                        tmem_ld16(dt + (uint32_t)j0, v);
+            const PackInfo &pi = pis[p];
+            const int t = pi.qtask[q];
+            const bool product = pi.kmax > 0;
+            if (t >= 0) {
+                const TaskRec &rc = recs[t];
+                const int r = row - (int)rc.nbm;           // this thread's row of C
+                const bool valid = r < (int)rc.M;
+                const int N = rc.N;
+                const float alpha = (float)rc.alpha, beta = (float)rc.beta;
+                const bool readc = (rc.flags & kFlagReadC) != 0;
+                float *Cp = reinterpret_cast<float *>(rc.C) + r;
+                const int64_t ldc = rc.ldc;
+                const char *c0p = T.S.base + rc.offC + r * 4;
+                const int csC = rc.csC;
+                const uint32_t dt = tmem + (uint32_t)(a * kTcMaxCols + (int)rc.nbn) + lane_base;
+                const int nchunk = (N + 15) >> 4;
+                for (int cb = 0; cb < nchunk; cb += 2) {
+                    uint32_t v[32];
+                    if (product) {
+                        tmem_ld16<0>(dt + (uint32_t)(16 * cb), v);
+                        if (cb + 1 < nchunk)
+                            tmem_ld16<16>(dt + (uint32_t)(16 * cb + 16), v);
+                        tmem_wait_ld(v);
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 16; ++u)
-                            v[u] = 0.f;
+                        for (int e = 0; e < 32; ++e)
+                            v[e] = 0u;
                     }
-                    if (mine) {
-                        // columns j0.. of the tile are columns j0-Cc.. of C
-                        const int jlo = max(j0, Cc) - Cc, jhi = min(j0 + 16, Cc + N) - Cc;
-                        float *cp = C + jlo * ldc;
-                        const char *c0p = c0 + jlo * csC;
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int j = j0 + u - Cc;
-                            if (j >= jlo && j < jhi) {
-                                float c = alpha * v[u];
-                                if (readc)
-                                    c = fmaf(beta, *reinterpret_cast<const float *>(c0p), c);
-                                *cp = c;
-                                cp += ldc;
-                                c0p += csC;
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (cb + cc < nchunk) {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const int j = 16 * (cb + cc) + u;
+                                if (j < N && valid) {
+                                    float x = alpha * __uint_as_float(v[16 * cc + u]);
+                                    if (readc)
+                                        x = fmaf(beta, *reinterpret_cast<const float *>(c0p + j * csC), x);
+                                    Cp[j * ldc] = x;
+                                }
                             }
                         }
                     }
@@ -634,7 +554,6 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(T.acc_empty(a));
-            a ^= 1;
         }
         __syncwarp();
         if (lane == 0)
@@ -651,6 +570,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
     T.S.sbase = smem_addr(smem_tc);
     T.S.ring_off = (uint32_t)tc_ring_offset<P>();
     T.S.ring_bytes = (uint32_t)tc_ring_bytes<P>();
+    T.S.pinfo_off = (uint32_t)kTcPackInfo;
+    T.S.cbar_off = (uint32_t)kTcBarCFull;
     const int warp = threadIdx.x / 32;
     if (threadIdx.x < kNumSlots * kMaxGroupTasks)
         mbar_init(T.S.task(threadIdx.x / kMaxGroupTasks, threadIdx.x % kMaxGroupTasks), 1);
@@ -658,12 +579,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
         for (int s = 0; s < kNumSlots; ++s) {
             mbar_init(T.S.full(s), 1);
             mbar_init(T.S.empty(s), kTcConvWarps + kTcEpiWarps);
+            mbar_init(T.S.cfull(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kTcStages; ++b) {
             mbar_init(T.op_full(b), kTcConvWarps);
             mbar_init(T.op_empty(b), 1);
-            mbar_init(T.acc_full(b), 1);
-            mbar_init(T.acc_empty(b), kTcEpiWarps);
+        }
+        for (int a = 0; a < kTcAccs; ++a) {
+            mbar_init(T.acc_full(a), 1);
+            mbar_init(T.acc_empty(a), kTcEpiWarps / 2);
         }
         fence_barrier_init();
     }
@@ -673,14 +597,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem_tc + kTcTmemSlot);
-    if (warp < kTcConvWarps)
+    if (warp < kTcConvWarps) {
         tc_converters<P>(KP, T, warp);
-    else if (warp < kTcConvWarps + kTcEpiWarps)
+    } else if (warp < kTcConvWarps + kTcEpiWarps) {
         tc_epilogue_warps<P>(KP, T, warp - kTcConvWarps, tmem);
-    else if (warp == kTcWarpProducer)
-        producer_loop<4>(KP, T.S);
-    else
-        tc_mma_warp<P>(KP, T, tmem);
+    } else if (warp == kTcWarpProducer) {
+        producer_loop<4, true>(KP, T.S);
+    } else {
+        if (lane_id() == 0)
+            tc_mma_thread<P>(KP, T, tmem);
+        __syncwarp();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -129,6 +129,36 @@ def test_edge_cases(dtype):
         assert np.array_equal(C[gi], (b.C[gi] * dtype(scale)).astype(dtype))
 
 
+# Small by MNK, but with one side far beyond a warp block or a stage: the
+# planner cuts such instances into row and column pieces (Sec. I bounds
+# cbrt(MNK), not the single sizes).
+PIECE_SHAPES = [  # M, N, K, transA, transB
+    (2000, 256, 1, 0, 0), (512000, 1, 1, 0, 0), (1, 512000, 1, 0, 1), (300, 300, 5, 1, 1),
+    (129, 129, 30, 0, 1), (32768, 1, 1, 1, 0), (130, 70, 40, 0, 0), (70, 200, 36, 0, 1),
+]
+
+
+def piece_batch(dtype, seed):
+    rng = np.random.default_rng(seed)
+    M, N, K, ta, tb = (list(x) for x in zip(*PIECE_SHAPES))
+    n = len(M)
+    be = [0.5, 0.0, -1.0, 0.5, 2.0, 0.0, 1.0, 0.5]
+    b = W.make_batch(M, N, K, ta, tb, [1.5, 1.0, -2.0, 1.0, 0.5, 1.0, 1.0, -1.0], be, dtype, rng,
+                     pad=rng.integers(0, 3, (n, 3)), dist="int")
+    assert W.in_domain(b.M, b.N, b.K, b.transA, b.transB).all()
+    return b
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_instances_cut_into_pieces(dtype):
+    b = piece_batch(dtype, 14)
+    C, info = run_grouped(b)
+    assert info["tasks"] > b.count
+    err = compare(b, C)
+    assert err["exact"], err
+    assert padding_untouched(b, C)
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_large_leading_dimensions(dtype):
     """ld far above the rows: operands are staged column by column."""

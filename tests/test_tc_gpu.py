@@ -92,6 +92,19 @@ def test_edge_cases(prec):
     assert padding_untouched(b, C)
 
 
+@pytest.mark.parametrize("prec", sorted(PRECS))
+def test_instances_cut_into_pieces(prec):
+    """Rows and columns beyond one 128 x 128 MMA tile: every piece is its own
+    task of at most 128 x 128.  Integer inputs, so every path is exact."""
+    from .test_gemm_gpu import piece_batch
+    b = piece_batch(np.float32, 15)
+    C, info = run_grouped(b, PRECS[prec])
+    assert info["tasks"] > b.count
+    err = compare(b, C)
+    assert err["exact"], err
+    assert padding_untouched(b, C)
+
+
 def test_3xbf16_graph_replay(cuda):
     torch = cuda
     b = W.random_small(3000, seed=55, max_dim=60, pad_max=3, beta=np.zeros(3000))
