@@ -19,8 +19,8 @@
 //        kTcStages operand stages: X = Xh + Xl (BF16) for 3xBF16,
 //        RN-rounded TF32, or FP16, with zeros past the row's K;
 //   8-15 epilogue: warp 8+e reads quarter e&3 of the accumulator of every
-//        pack whose sequence number has parity e>>2, batching two 16-column
-//        tensor-memory loads per wait, and writes alpha*acc +
+//        pack whose sequence number is e>>2 modulo kTcEpiPhases, batching two
+//        16-column tensor-memory loads per wait, and writes alpha*acc +
 //        beta*C0 to exactly the task's elements;
 //   16   producer: streams stages into the shared-memory ring (shared with
 //        the CUDA-core kernel) and summarises each pack (PackInfo);
@@ -45,9 +45,11 @@ constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
 constexpr int kTcKC = 32;              // K per operand stage
 constexpr int kTcStages = 2;           // operand stages
 constexpr int kTcAccs = 4;             // accumulators of kTcMaxCols columns
-constexpr int kTcConvWarps = 8, kTcEpiWarps = 8;
-constexpr int kTcWarpProducer = 16, kTcWarpMma = 17;
-constexpr int kTcThreads = 576;
+constexpr int kTcConvWarps = 8;       // 4 for the rows of op(A), 4 for op(B)^T
+constexpr int kTcEpiWarps = 8;        // a multiple of 4: one per lane quarter and pack phase
+constexpr int kTcEpiPhases = kTcEpiWarps / 4;   // packs in flight in the epilogue per quarter
+constexpr int kTcWarpProducer = kTcConvWarps + kTcEpiWarps, kTcWarpMma = kTcWarpProducer + 1;
+constexpr int kTcThreads = 32 * (kTcWarpMma + 1);
 constexpr int kTcTmemCols = kTcAccs * kTcMaxCols;
 
 template <int P> struct TcTraits;
@@ -78,7 +80,7 @@ constexpr int kTcExtra = kSmemSlots + kNumSlots * kSlotBytes;
 constexpr int kTcBarOpFull = kTcExtra;          // [kTcStages], kTcConvWarps arrivals
 constexpr int kTcBarOpEmpty = kTcExtra + 32;    // [kTcStages], tcgen05.commit
 constexpr int kTcBarAccFull = kTcExtra + 64;    // [kTcAccs], tcgen05.commit
-constexpr int kTcBarAccEmpty = kTcExtra + 96;   // [kTcAccs], 4 epilogue-warp arrivals
+constexpr int kTcBarAccEmpty = kTcExtra + 96;   // [kTcAccs], 4 epilogue-warp arrivals (one per quarter)
 constexpr int kTcBarCFull = kTcExtra + 128;     // [kNumSlots], the stage's C copies
 constexpr int kTcTmemSlot = kTcExtra + 192;     // tcgen05.alloc result
 constexpr int kTcChunkInfo = kTcExtra + 256;    // [kTcStages] x 16 B
@@ -86,7 +88,8 @@ constexpr int kTcPackInfo = kTcExtra + 320;     // PackInfo[kNumSlots][kMaxGroup
 constexpr int kTcOperands = (kTcPackInfo + kNumSlots * kMaxGroupTasks * (int)sizeof(PackInfo) + 1023) & ~1023;
 static_assert(kTcExtra % 16 == 0, "barrier alignment");
 static_assert(kTcStages <= 4 && kTcAccs <= 4 && kNumSlots <= 8, "barrier space");
-static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps == 8, "accumulator rotation");
+static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps % 4 == 0 && kTcAccs % kTcEpiPhases == 0 &&
+                  kTcConvWarps % 4 == 0, "accumulator rotation, lane quarters");
 template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + kTcStages * tc_stage_bytes<P>(); }
 template <int P> IAAT_CE int tc_ring_bytes() { return (kSmemTotal - tc_ring_offset<P>()) & ~127; }
 // A stage may take at most a third of the ring, so three are in flight.
@@ -477,7 +480,7 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
     const Params &Pm = KP.p;
     const int lane = (int)lane_id();
     const int q = ew & 3;                           // tensor-memory lane quarter (= warp index mod 4)
-    const int half = ew >> 2;                       // packs of this sequence parity
+    const int phase = ew >> 2;                      // packs pk with pk % kTcEpiPhases == phase
     const int row = 32 * q + lane;                  // accumulator row (tensor-memory lane) of this thread
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     uint32_t pk = 0;                                // pack sequence number
@@ -496,7 +499,7 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
         const PackInfo *pis = T.S.pinfo(slot);
         const int npk = T.S.header(slot)->npacks;
         for (int p = 0; p < npk; ++p, ++pk) {
-            if ((int)(pk & 1u) != half)
+            if ((int)(pk % kTcEpiPhases) != phase)
                 continue;
             const int a = (int)(pk & (kTcAccs - 1));
             if (!warp_wait(T.acc_full(a), (pk / kTcAccs) & 1u)) {
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
         }
         for (int a = 0; a < kTcAccs; ++a) {
             mbar_init(T.acc_full(a), 1);
-            mbar_init(T.acc_empty(a), kTcEpiWarps / 2);
+            mbar_init(T.acc_empty(a), 4);
         }
         fence_barrier_init();
     }
