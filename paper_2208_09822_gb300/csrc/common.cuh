@@ -45,6 +45,13 @@ struct alignas(16) TaskDesc {
 static_assert(sizeof(TaskDesc) == 64, "TaskDesc layout");
 constexpr uint8_t kFlagReadC = 1;
 
+// alpha or beta of a task record, in the plan's precision: FP64 plans read
+// the double, FP32 plans the float (no FP64 conversion on the device).
+union RecScalar {
+    double d;
+    float f;
+};
+
 // What the consumer warps see of a task once its operands sit in shared
 // memory: element (i, j) of the stored X is at byte off + j*cs + i*esz.
 struct alignas(16) TaskRec {
@@ -54,9 +61,22 @@ struct alignas(16) TaskRec {
     int32_t csA, csB, csC;
     int16_t M, N, K;
     uint8_t ta, tb, variant, flags, nbm, nbn;
-    double alpha, beta;
+    RecScalar alpha, beta;
 };
 static_assert(sizeof(TaskRec) == 64, "TaskRec layout");
+
+IAAT_HD void set_scalars(TaskRec &r, double alpha, double beta, int esz)
+{
+    r.alpha.d = 0.0;
+    r.beta.d = 0.0;
+    if (esz == 4) {
+        r.alpha.f = (float)alpha;
+        r.beta.f = (float)beta;
+    } else {
+        r.alpha.d = alpha;
+        r.beta.d = beta;
+    }
+}
 
 // Tensor-core kernel: one pack (one 128-row MMA tile) of a stage, as the
 // producer summarises it for the converter, MMA and epilogue roles.

@@ -200,7 +200,7 @@ __device__ void producer_dyn(const KParams &KP, const SmemMap &S)
             r.M = d.M; r.N = d.N; r.K = d.K;
             r.ta = d.ta; r.tb = d.tb; r.variant = d.variant; r.flags = d.flags;
             r.nbm = d.nbm; r.nbn = d.nbn;
-            r.alpha = d.alpha; r.beta = d.beta;
+            set_scalars(r, d.alpha, d.beta, ESZ);
             S.recs(slot)[lane] = r;
         }
         hd->prefix[lane] = has ? nbi : 0x7fffffff;
@@ -530,7 +530,14 @@ __device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, in
     }
 
     // epilogue: C = alpha*acc + beta*C0, exact elements only
-    const T alpha = (T)r.alpha, beta = (T)r.beta;
+    T alpha, beta;
+    if constexpr (ESZ == 4) {
+        alpha = r.alpha.f;
+        beta = r.beta.f;
+    } else {
+        alpha = r.alpha.d;
+        beta = r.beta.d;
+    }
     const bool readc = (r.flags & kFlagReadC) != 0;
     const char *Craw = smem + r.offC;
     T *Cg = reinterpret_cast<T *>(r.C);

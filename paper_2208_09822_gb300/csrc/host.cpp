@@ -565,7 +565,7 @@ iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vecto
                 r.M = d.M; r.N = d.N; r.K = d.K;
                 r.ta = d.ta; r.tb = d.tb; r.variant = d.variant; r.flags = d.flags;
                 r.nbm = d.nbm; r.nbn = d.nbn;
-                r.alpha = d.alpha; r.beta = d.beta;
+                set_scalars(r, d.alpha, d.beta, esz);
                 nbi += (int)d.nbm * (int)d.nbn;
                 hd.prefix[t] = nbi;
                 tx[t] = s.a.tx + s.b.tx + (tc ? 0u : s.c.tx);

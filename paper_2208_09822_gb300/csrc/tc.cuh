@@ -417,6 +417,7 @@ __device__ void tc_mma_thread(const KParams &KP, const TcSmem &T, uint32_t tmem)
     uint32_t bpar = 0;
     uint32_t pk = 0;     // packs completed
     int total = 0;       // chunks consumed (each sends one commit to its stage's op_empty)
+    const uint32_t ops = smem_addr(T.S.base + kTcOperands);
     for (;;) {
         if (!mbar_wait(T.op_full(b), bpar, kWaitLimitNs)) {
             set_error(Pm.err, kErrTimeoutFull);
@@ -436,20 +437,25 @@ __device__ void tc_mma_thread(const KParams &KP, const TcSmem &T, uint32_t tmem)
         if (ci.kc > 0) {
             const uint32_t d = tmem + (uint32_t)(a * kTcMaxCols);
             const uint32_t idesc = tc_idesc<P>(ci.nt);
-            const uint32_t base = smem_addr(T.S.base + kTcOperands + b * tc_stage_bytes<P>());
-            const uint32_t a0 = base, a1 = base + OPB;
-            const uint32_t b0 = base + TcTraits<P>::kTerms * OPB, b1 = b0 + OPB;
-            const bool first = (ci.flags & kChunkFirst) != 0;
+            const uint32_t base = ops + (uint32_t)(b * tc_stage_bytes<P>());
+            // descriptors of the chunk's first K step; each step moves 256
+            // bytes (two core matrices) along K, 16 in the address field
+            uint64_t da0 = smem_desc(base, 128, SBO), db0 = smem_desc(base + TcTraits<P>::kTerms * OPB, 128, SBO);
+            uint64_t da1 = da0 + (OPB >> 4), db1 = db0 + (OPB >> 4);
+            uint32_t accum = (ci.flags & kChunkFirst) ? 0u : 1u;
             for (int ks = 0; ks < ci.kc / KS; ++ks) {
-                const uint32_t o = (uint32_t)ks * 256u;   // two core matrices along K
-                const uint32_t accum = (first && ks == 0) ? 0u : 1u;
                 if constexpr (P == kTc3xBF16) {
-                    tc_mma<P>(d, smem_desc(a1 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
-                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b1 + o, 128, SBO), idesc, 1);
-                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, 1);
+                    tc_mma<P>(d, da1, db0, idesc, accum);
+                    tc_mma<P>(d, da0, db1, idesc, 1u);
+                    tc_mma<P>(d, da0, db0, idesc, 1u);
+                    da1 += 16;
+                    db1 += 16;
                 } else {
-                    tc_mma<P>(d, smem_desc(a0 + o, 128, SBO), smem_desc(b0 + o, 128, SBO), idesc, accum);
+                    tc_mma<P>(d, da0, db0, idesc, accum);
                 }
+                da0 += 16;
+                db0 += 16;
+                accum = 1u;
             }
         }
         tc_commit(T.op_empty(b));
@@ -516,7 +522,7 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
                 const int r = row - (int)rc.nbm;           // this thread's row of C
                 const bool valid = r < (int)rc.M;
                 const int N = rc.N;
-                const float alpha = (float)rc.alpha, beta = (float)rc.beta;
+                const float alpha = rc.alpha.f, beta = rc.beta.f;
                 const bool readc = (rc.flags & kFlagReadC) != 0;
                 float *Cp = reinterpret_cast<float *>(rc.C) + r;
                 const int64_t ldc = rc.ldc;
@@ -536,19 +542,24 @@ __device__ void tc_epilogue_warps(const KParams &KP, const TcSmem &T, int ew, ui
                         for (int e = 0; e < 32; ++e)
                             v[e] = 0u;
                     }
+                    // all of a chunk's C0 loads first, then its stores:
+                    // predicated, so nothing waits on a branch
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
-                        if (cb + cc < nchunk) {
+                        const int j0 = 16 * (cb + cc);
+                        if (j0 < N) {
+                            const int jn = min(16, N - j0);
+                            const char *c0c = c0p + j0 * csC;
+                            float c0v[16];
 #pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const int j = 16 * (cb + cc) + u;
-                                if (j < N && valid) {
-                                    float x = alpha * __uint_as_float(v[16 * cc + u]);
-                                    if (readc)
-                                        x = fmaf(beta, *reinterpret_cast<const float *>(c0p + j * csC), x);
-                                    Cp[j * ldc] = x;
-                                }
-                            }
+                            for (int u = 0; u < 16; ++u)
+                                c0v[u] = (readc && valid && u < jn) ? *reinterpret_cast<const float *>(c0c + u * csC)
+                                                                      : 0.0f;
+                            float *cpc = Cp + j0 * ldc;
+#pragma unroll
+                            for (int u = 0; u < 16; ++u)
+                                if (valid && u < jn)
+                                    cpc[u * ldc] = fmaf(beta, c0v[u], alpha * __uint_as_float(v[16 * cc + u]));
                         }
                     }
                 }
