@@ -391,7 +391,7 @@ __device__ __forceinline__ int swz(int m, int kk)
 // raw(m, kk) = src + m*sm + kk*sk.  Elements with m >= mh or kk >= kc are 0.
 // MFAST: lanes run along m (raw contiguous in m), else along kk.
 template <typename T, int BM, int KC, bool MFAST>
-__device__ __noinline__ void repack(T *X, const char *src, int sm, int sk, int mh, int kc, int kcp)
+__device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, int mh, int kc, int kcp)
 {
     constexpr int VE = 16 / (int)sizeof(T);
     const int lane = (int)lane_id();
