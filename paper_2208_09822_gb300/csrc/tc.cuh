@@ -11,10 +11,11 @@
 // read by the warps of SM sub-partition q: one task per quarter spreads each
 // pack's epilogue over all four sub-partitions.
 //
-// Warp roles (18 warps):
+// Warp roles (20 warps; 16 and 17 only pad, see kTcWarpProducer):
 //   0-7  converters: per 32-wide K-chunk of a pack, every thread converts one
 //        row of a 128-row operand tile -- warps 0-3 the rows of op(A) (one
-//        quarter each), warps 4-7 the rows of op(B)^T -- from the staged FP32
+//        quarter each), warps 4-7 those of op(B)^T (in reverse order of
+//        quarters) -- from the staged FP32
 //        data into the canonical K-major (no swizzle) layout of one of
 //        kTcStages operand stages: X = Xh + Xl (BF16) for 3xBF16,
 //        RN-rounded TF32, or FP16, with zeros past the row's K;
@@ -22,9 +23,9 @@
 //        pack whose sequence number is e>>2 modulo kTcEpiPhases, batching two
 //        16-column tensor-memory loads per wait, and writes alpha*acc +
 //        beta*C0 to exactly the task's elements;
-//   16   producer: streams stages into the shared-memory ring (shared with
-//        the CUDA-core kernel) and summarises each pack (PackInfo);
-//   17   MMA: one lane issues each chunk's MMAs into one of kTcAccs
+//   18   producer: streams stages into the shared-memory ring (shared with
+//        the CUDA-core kernel) and copies each pack's summary (PackInfo);
+//   19   MMA: one lane issues each chunk's MMAs into one of kTcAccs
 //        accumulators and commits them to mbarriers that free the operand
 //        stage and, after a pack's last chunk, hand the accumulator over.
 // Conversion of the next chunks, the MMAs of this one and the epilogue of up
@@ -48,7 +49,12 @@ constexpr int kTcAccs = 4;             // accumulators of kTcMaxCols columns
 constexpr int kTcConvWarps = 8;       // 4 for the rows of op(A), 4 for op(B)^T
 constexpr int kTcEpiWarps = 8;        // a multiple of 4: one per lane quarter and pack phase
 constexpr int kTcEpiPhases = kTcEpiWarps / 4;   // packs in flight in the epilogue per quarter
-constexpr int kTcWarpProducer = kTcConvWarps + kTcEpiWarps, kTcWarpMma = kTcWarpProducer + 1;
+// The producer and the MMA thread run on SM sub-partitions 2 and 3 (warp
+// index mod 4), whose converter and epilogue warps -- lane quarters 2 and 3
+// of a pack, the ones a pack fills last -- have the least work; the two warps
+// before them only pad the block to get there.
+constexpr int kTcWarpProducer = kTcConvWarps + kTcEpiWarps + 2, kTcWarpMma = kTcWarpProducer + 1;
+static_assert(kTcWarpProducer % 4 == 2 && kTcWarpMma % 4 == 3, "role placement");
 constexpr int kTcThreads = 32 * (kTcWarpMma + 1);
 constexpr int kTcTmemCols = kTcAccs * kTcMaxCols;
 
@@ -88,8 +94,8 @@ constexpr int kTcPackInfo = kTcExtra + 320;     // PackInfo[kNumSlots][kMaxGroup
 constexpr int kTcOperands = (kTcPackInfo + kNumSlots * kMaxGroupTasks * (int)sizeof(PackInfo) + 1023) & ~1023;
 static_assert(kTcExtra % 16 == 0, "barrier alignment");
 static_assert(kTcStages <= 4 && kTcAccs <= 4 && kNumSlots <= 8, "barrier space");
-static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps % 4 == 0 && kTcAccs % kTcEpiPhases == 0 &&
-                  kTcConvWarps % 4 == 0, "accumulator rotation, lane quarters");
+static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps % 4 == 0 && kTcConvWarps % 4 == 0,
+              "accumulator rotation, lane quarters");
 template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + kTcStages * tc_stage_bytes<P>(); }
 template <int P> IAAT_CE int tc_ring_bytes() { return (kSmemTotal - tc_ring_offset<P>()) & ~127; }
 // A stage may take at most a third of the ring, so three are in flight.
@@ -271,7 +277,10 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
     constexpr int VPR = tc_vpr<P>();
     constexpr int KS = TcTraits<P>::kKStep;
     const int side = cw >> 2;                 // 0: rows of op(A), 1: rows of op(B)^T
-    const int row = 32 * (cw & 3) + lane;     // this thread's row of the operand tile
+    // this thread's row of the operand tile: op(A) rows 32q.. run on sub-
+    // partition q, op(B)^T rows 32(3-q).. too, so the busy low rows of both
+    // operands (packs fill from row 0) share the sub-partitions evenly
+    const int row = 32 * (side == 0 ? (cw & 3) : 3 - (cw & 3)) + lane;
     const uint32_t row_off = (uint32_t)((row >> 3) * tc_sbo<P>() + (row & 7) * 16);
     int b = 0;
     uint32_t bpar = 0;     // parity of the operand stages' current round
@@ -615,6 +624,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) grouped_tc_kernel(const __grid_
         tc_converters<P>(KP, T, warp);
     } else if (warp < kTcConvWarps + kTcEpiWarps) {
         tc_epilogue_warps<P>(KP, T, warp - kTcConvWarps, tmem);
+    } else if (warp < kTcWarpProducer) {
+        // padding warps: nothing to do until the final barrier
     } else if (warp == kTcWarpProducer) {
         producer_loop<4, true>(KP, T.S);
     } else {
