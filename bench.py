@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=200_000,
                     help="instances of the uneven batch (smaller only for profiling captures)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan with the built-in cost model instead of tuning each path first")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -230,6 +232,18 @@ def main():
         dist.barrier()
     from paper_2208_09822_gb300 import iaat
     from paper_2208_09822_gb300 import workloads as W
+
+    # the autotuner (Sec. IV's install-time tuning, done at start-up here):
+    # per-variant costs and the stage size of every timed path, measured on
+    # this GPU before anything is timed; skipped when a tuning cache is given
+    tuned = "built-in cost model"
+    if not args.no_autotune and not os.environ.get("IAAT_TUNE_CACHE"):
+        t0 = time.time()
+        for name in dict.fromkeys([args.precision] + list(args.compare)):
+            iaat.iaat_autotune(iaat.IAAT_F32, PRECISIONS[name], None)
+        tuned = f"autotuned at start-up ({time.time() - t0:.1f} s, outside the timed region)"
+    elif os.environ.get("IAAT_TUNE_CACHE"):
+        tuned = "tuning cache " + os.environ["IAAT_TUNE_CACHE"]
 
     batch = W.uneven(count=args.instances)
     tA = torch.from_numpy(batch.A).to(dev)
@@ -355,7 +369,7 @@ def main():
                        "l2": "inputs larger than L2 (pools %.2f GB > 129 MB); no flush" %
                              ((batch.A.nbytes + batch.B.nbytes + batch.C.nbytes) / 1e9),
                        "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
-                       "grid": info["grid"]},
+                       "grid": info["grid"], "tuning": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth",

@@ -283,12 +283,13 @@ struct Params {
 
 // Kernel parameters: either plan arrays in global memory, or (single call)
 // up to kInline tasks carried inline in the parameter block.
-constexpr int kInline = 8;
+constexpr int kInline = 32;
 struct KParams {
     Params p;
     TaskDesc inline_tasks[kInline];
     int32_t inline_gbeg[kInline + 1];
 };
+static_assert(sizeof(KParams) <= 4096, "kernel parameter block");
 
 constexpr int32_t kErrTimeoutFull = 1;
 constexpr int32_t kErrTimeoutEmpty = 2;

@@ -113,7 +113,11 @@ struct TileChoice {
     double cost;
 };
 
-static TileChoice choose_tiling(int esz, int M, int N, int K, int force_variant)
+// scaled: weigh the variants by the autotuner's measured scales (the
+// CUDA-core kernel); the tensor-core planner only uses the cost as an
+// ordering key and takes the plain model, so that tuning the CUDA-core
+// kernel does not reorder tensor-core stages.
+static TileChoice choose_tiling(int esz, int M, int N, int K, int force_variant, bool scaled = true)
 {
     int nv;
     const Variant *vs = variants(esz, &nv);
@@ -125,7 +129,7 @@ static TileChoice choose_tiling(int esz, int M, int N, int K, int force_variant)
         const int nbm = std::max(1, (M + bm - 1) / bm), nbn = std::max(1, (N + bn - 1) / bn);
         if (nbm > 255 || nbn > 255)
             continue;
-        const double c = (double)nbm * nbn * block_cost(vs[v], esz, K) * tuning().variant_scale(esz, v);
+        const double c = (double)nbm * nbn * block_cost(vs[v], esz, K) * (scaled ? tuning().variant_scale(esz, v) : 1.0);
         if (c < best.cost)
             best = TileChoice{v, nbm, nbn, c};
     }
@@ -356,9 +360,11 @@ bool choose_split(const iaat_gemm_desc_t &g, int esz, int Keff, uint32_t cap, in
     }
 }
 
-// Build the tasks of one instance: one, or its pieces.
+// Build the tasks of one instance: one, or its pieces.  piece > 0: cut C into
+// pieces of at most piece x piece as well (the single-call path spreads one
+// instance over several SMs that way).
 iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool tc, int force_variant, uint32_t cap,
-                         std::vector<HostTask> &out, int64_t *blocks_out)
+                         std::vector<HostTask> &out, int64_t *blocks_out, int piece = 0)
 {
     const int M = g.M, N = g.N;
     if (M == 0 || N == 0)
@@ -367,7 +373,9 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool t
     if (Keff == 0 && g.beta == 1.0)
         return IAAT_OK;   // C = 1*C: nothing to do
     int pm = 1, pn = 1;
-    if (!choose_split(g, esz, Keff, cap, tc ? kTcPackRows : kPieceRows, tc ? kTcPackCols : kPieceCols, pm, pn))
+    const int mcap = piece > 0 ? piece : (tc ? kTcPackRows : kPieceRows);
+    const int ncap = piece > 0 ? piece : (tc ? kTcPackCols : kPieceCols);
+    if (!choose_split(g, esz, Keff, cap, mcap, ncap, pm, pn))
         return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage (M=%d N=%d K=%d)",
                     (long long)idx, M, N, g.K);
     for (int i = 0; i < pm; ++i) {
@@ -377,7 +385,7 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool t
             int c0, w;
             piece_range(N, pn, j, c0, w);
             TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
-            const TileChoice t = choose_tiling(esz, h, w, Keff, force_variant);
+            const TileChoice t = choose_tiling(esz, h, w, Keff, force_variant, !tc);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
             d.nbn = (uint8_t)t.nbn;
@@ -846,8 +854,20 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     iaat_gemm_desc_t g{M, N, K, lda, ldb, ldc, ta, tb, alpha, beta, A, B, C};
     std::vector<HostTask> tasks;
     int64_t nb = 0;
+    // one instance per call: an FP64 instance is cut into pieces of about
+    // 16 x 16 of C, as many as the parameter block holds, so that they run on
+    // that many SMs -- one SM's DFMA rate (about 8 GFLOP/s) would otherwise
+    // set the latency (measured: 80^3 from 92 to 36 us).  FP32 is not cut: at
+    // 60x that rate the extra CTAs and operand re-reads cost more than they
+    // save (48^3: 8 -> 15 us when cut).
+    int piece = 0;
+    if (esz == 8) {
+        piece = 16;
+        while (piece < kPieceRows && (int64_t)((M + piece - 1) / piece) * ((N + piece - 1) / piece) > kInline)
+            piece *= 2;
+    }
     st = make_tasks(0, g, esz, false, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks,
-                    &nb);
+                    &nb, piece);
     if (st != IAAT_OK)
         return st;
     if (tasks.empty())
