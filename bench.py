@@ -206,6 +206,8 @@ def main():
     ap.add_argument("--compare", default="ffma", type=lambda v: [x for x in v.split(",") if x],
                     help="comma-separated paths timed beside the headline (plain FP32 by default)")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="instance ranges the end-to-end leg pipelines copies and launches over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=200_000,
                     help="instances of the uneven batch (smaller only for profiling captures)")
@@ -313,34 +315,101 @@ def main():
     achieved = abytes / (ms * 1e-3) / 1e9
     roof_gflops = abytes and flops / abytes * NOMINAL_HBM_GBS
 
-    # end to end through the C ABI: pinned host -> device, launch, C -> host
+    # end to end through the C ABI from pinned host buffers.  Serial: every
+    # step copies the pools in, launches the plan, copies C out, one after the
+    # other.  Pipelined (the reported number): the batch is cut into
+    # contiguous instance ranges, one plan each, and on three streams the
+    # copy-in of range c+1, the launch of range c and the copy-out of range c-1
+    # overlap; a range is copied in again only after its previous copy-out.
+    from paper_2208_09822_gb300.shard import instance_cost, shard_bounds
     hA = torch.from_numpy(batch.A).pin_memory()
     hB = torch.from_numpy(batch.B).pin_memory()
     hC = torch.from_numpy(batch.C).pin_memory()
     hOut = torch.empty_like(hC).pin_memory()
     h2d = hA.numel() * hA.element_size() + hB.numel() * hB.element_size() + hC.numel() * hC.element_size()
     d2h = hOut.numel() * hOut.element_size()
-    with torch.cuda.stream(stream):
-        tA.copy_(hA, non_blocking=True); tB.copy_(hB, non_blocking=True); tC.copy_(hC, non_blocking=True)
-        iaat.iaat_gemm_grouped(plan, stream)
-        hOut.copy_(tC, non_blocking=True)
-    torch.cuda.synchronize()
     args.e2e_steps = max(1, args.e2e_steps)
-    if world > 1:
-        dist.barrier()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(args.e2e_steps):
-            tA.copy_(hA, non_blocking=True)
-            tB.copy_(hB, non_blocking=True)
-            tC.copy_(hC, non_blocking=True)
+
+    def e2e_serial():
+        with torch.cuda.stream(stream):
+            tA.copy_(hA, non_blocking=True); tB.copy_(hB, non_blocking=True); tC.copy_(hC, non_blocking=True)
             iaat.iaat_gemm_grouped(plan, stream)
             hOut.copy_(tC, non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.e2e_steps):
+                tA.copy_(hA, non_blocking=True)
+                tB.copy_(hB, non_blocking=True)
+                tC.copy_(hC, non_blocking=True)
+                iaat.iaat_gemm_grouped(plan, stream)
+                hOut.copy_(tC, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        return f0.elapsed_time(f1) / args.e2e_steps
+
+    def e2e_pipelined(nchunks):
+        n = batch.count
+        cost = instance_cost(batch.M, batch.N, batch.K, batch.beta != 0)
+        ranges = [(b0, b1) for b0, b1 in shard_bounds(cost, nchunks) if b1 > b0]
+        parts = []
+        for b0, b1 in ranges:
+            span = lambda off, pool: (int(off[b0]), int(off[b1]) if b1 < n else pool.size)
+            parts.append((iaat.iaat_plan_create(descs[b0:b1], iaat.IAAT_F32, PRECISIONS[args.precision]),
+                          span(batch.offA, batch.A), span(batch.offB, batch.B), span(batch.offC, batch.C)))
+        s_in = torch.cuda.Stream(device=dev)
+        s_out = torch.cuda.Stream(device=dev)
+        ev_in = [torch.cuda.Event() for _ in parts]
+        ev_cmp = [torch.cuda.Event() for _ in parts]
+        ev_out = [torch.cuda.Event() for _ in parts]
+
+        def step(first):
+            for c, (pl, ra, rb, rc) in enumerate(parts):
+                if not first:
+                    s_in.wait_event(ev_out[c])
+                with torch.cuda.stream(s_in):
+                    tA[ra[0]:ra[1]].copy_(hA[ra[0]:ra[1]], non_blocking=True)
+                    tB[rb[0]:rb[1]].copy_(hB[rb[0]:rb[1]], non_blocking=True)
+                    tC[rc[0]:rc[1]].copy_(hC[rc[0]:rc[1]], non_blocking=True)
+                    ev_in[c].record(s_in)
+                stream.wait_event(ev_in[c])
+                iaat.iaat_gemm_grouped(pl, stream)
+                ev_cmp[c].record(stream)
+                s_out.wait_event(ev_cmp[c])
+                with torch.cuda.stream(s_out):
+                    hOut[rc[0]:rc[1]].copy_(tC[rc[0]:rc[1]], non_blocking=True)
+                    ev_out[c].record(s_out)
+
+        step(True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s_in)
+        stream.wait_event(f0)
+        s_out.wait_event(f0)
+        for _ in range(args.e2e_steps):
+            step(False)
+        s_out.wait_stream(s_in)
+        s_out.wait_stream(stream)
+        f1.record(s_out)
+        torch.cuda.synchronize()
+        for pl, *_ in parts:
+            iaat.iaat_plan_check(pl, stream)
+            pl.destroy()
+        return f0.elapsed_time(f1) / args.e2e_steps, len(parts)
+
+    e2e_serial_ms = e2e_serial()
+    iaat.iaat_plan_check(plan, stream)
+    e2e_ms, e2e_parts = e2e_pipelined(args.e2e_chunks)
+    # the pipelined result must equal the one-plan result (same inputs, same plans per instance)
+    if rank == 0 and not np.array_equal(hOut.numpy(), first_result):
+        print("warning: pipelined end-to-end result differs from the single launch", file=sys.stderr)
     iaat.iaat_plan_check(plan, stream)
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
@@ -378,7 +447,9 @@ def main():
                          "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                    "pipelined_ranges": e2e_parts,
+                    "serial_value": flops * world / (e2e_serial_ms * 1e-3) / 1e9},
             "paths": paths,
             "error": errs.get(args.precision),
             "gpu_launches": args.steps * info["kernels"],
