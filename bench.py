@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--compare", default="ffma", type=lambda v: [x for x in v.split(",") if x],
                     help="comma-separated paths timed beside the headline (plain FP32 by default)")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--e2e-chunks", type=int, default=8,
+    ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="instance ranges the end-to-end leg pipelines copies and launches over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=200_000,
