@@ -46,7 +46,7 @@ constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
 constexpr int kTcKC = 32;              // K per operand stage
 constexpr int kTcStages = 2;           // operand stages
 constexpr int kTcAccs = 4;             // accumulators of kTcMaxCols columns
-constexpr int kTcConvWarps = 8;       // 4 for the rows of op(A), 4 for op(B)^T
+constexpr int kTcConvWarps = 8;       // 4 for the rows of op(A), 4 for op(B)^T (16: two per row)
 constexpr int kTcEpiWarps = 8;        // a multiple of 4: one per lane quarter and pack phase
 constexpr int kTcEpiPhases = kTcEpiWarps / 4;   // packs in flight in the epilogue per quarter
 // The producer and the MMA thread run on SM sub-partitions 2 and 3 (warp
@@ -94,8 +94,8 @@ constexpr int kTcPackInfo = kTcExtra + 320;     // PackInfo[kNumSlots][kMaxGroup
 constexpr int kTcOperands = (kTcPackInfo + kNumSlots * kMaxGroupTasks * (int)sizeof(PackInfo) + 1023) & ~1023;
 static_assert(kTcExtra % 16 == 0, "barrier alignment");
 static_assert(kTcStages <= 4 && kTcAccs <= 4 && kNumSlots <= 8, "barrier space");
-static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps % 4 == 0 && kTcConvWarps % 4 == 0,
-              "accumulator rotation, lane quarters");
+static_assert((kTcAccs & (kTcAccs - 1)) == 0 && kTcEpiWarps % 4 == 0 && (kTcConvWarps == 8 || kTcConvWarps == 16),
+              "accumulator rotation, lane quarters, converter split");
 template <int P> IAAT_CE int tc_ring_offset() { return kTcOperands + kTcStages * tc_stage_bytes<P>(); }
 template <int P> IAAT_CE int tc_ring_bytes() { return (kSmemTotal - tc_ring_offset<P>()) & ~127; }
 // A stage may take at most a third of the ring, so three are in flight.
@@ -276,7 +276,9 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
     constexpr int OPB = tc_operand_bytes<P>();
     constexpr int VPR = tc_vpr<P>();
     constexpr int KS = TcTraits<P>::kKStep;
-    const int side = cw >> 2;                 // 0: rows of op(A), 1: rows of op(B)^T
+    const int side = (cw >> 2) & 1;           // 0: rows of op(A), 1: rows of op(B)^T
+    const int gfirst = cw >> 3;               // with 16 converter warps, two share each row:
+    constexpr int GSTEP = kTcConvWarps / 8;   // this warp takes K-groups gfirst, gfirst + GSTEP, ...
     // this thread's row of the operand tile: op(A) rows 32q.. run on sub-
     // partition q, op(B)^T rows 32(3-q).. too, so the busy low rows of both
     // operands (packs fill from row 0) share the sub-partitions evenly
@@ -356,7 +358,7 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
                 if (valid && kc > 0) {
                     const int ng = kc / VPR;
 #pragma unroll 1
-                    for (int gi = 0; gi < ng; ++gi) {
+                    for (int gi = gfirst; gi < ng; gi += GSTEP) {
                         const int kb = k0 + gi * VPR;
                         const char *q = src + kb * sk;
                         float x[8];
