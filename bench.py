@@ -33,7 +33,7 @@ METRIC = "small-GEMM GFLOP/s & roofline % (uneven batch), TC split vs plain FP32
 WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT/TN/TT uniform "
             "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
 NOMINAL_HBM_GBS = 8000.0
-PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3}
+PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
 
 
 def env_rank():

@@ -54,12 +54,17 @@ typedef enum { IAAT_F32 = 0, IAAT_F64 = 1 } iaat_dtype_t;
  * 3XBF16:  tcgen05 tensor cores, X = Xh + Xl with Xh = bf16(X), Xl =
  *          bf16(X - Xh); Ah*Bh + Ah*Bl + Al*Bh accumulated in FP32.
  * TF32:    tcgen05 kind::tf32 on round-to-nearest TF32 inputs, FP32 accumulate.
- * FP16:    tcgen05 kind::f16 on FP16-rounded inputs, FP32 accumulate. */
+ * FP16:    tcgen05 kind::f16 on FP16-rounded inputs, FP32 accumulate.
+ * 6XBF16:  tcgen05 tensor cores, X = Xh + Xm + Xl (three BF16 terms, each
+ *          the rounding of what the previous ones leave); the six products
+ *          of order up to two (mm, lh, hl, mh, hm, hh) accumulated in FP32,
+ *          for FFMA-like accuracy per instance also at tiny K. */
 typedef enum {
     IAAT_PREC_DEFAULT = 0,
     IAAT_PREC_3XBF16 = 1,
     IAAT_PREC_TF32 = 2,
-    IAAT_PREC_FP16 = 3
+    IAAT_PREC_FP16 = 3,
+    IAAT_PREC_6XBF16 = 4
 } iaat_precision_t;
 
 typedef enum {

@@ -249,9 +249,9 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][5];
+bool g_prepared[64][6];
 
-// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2.. = tcgen05 precision (kind - 1)
+// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2..5 = tcgen05 precision (kind - 1)
 iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
@@ -631,7 +631,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         return fail(IAAT_ERR_INVALID_VALUE, "bad descriptor array");
     if (dtype != IAAT_F32 && dtype != IAAT_F64)
         return fail(IAAT_ERR_INVALID_VALUE, "unknown dtype %d", (int)dtype);
-    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_FP16)
+    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_6XBF16)
         return fail(IAAT_ERR_INVALID_VALUE, "unknown precision %d", (int)precision);
     if (precision != IAAT_PREC_DEFAULT && dtype == IAAT_F64)
         return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");

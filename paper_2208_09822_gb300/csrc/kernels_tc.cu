@@ -14,6 +14,8 @@ cudaError_t prepare_tc(int precision)
         return cudaFuncSetAttribute(grouped_tc_kernel<kTcTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
     case kTcFP16:
         return cudaFuncSetAttribute(grouped_tc_kernel<kTcFP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
+    case kTc6xBF16:
+        return cudaFuncSetAttribute(grouped_tc_kernel<kTc6xBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
     default:
         return cudaErrorInvalidValue;
     }
@@ -33,6 +35,9 @@ cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t s
     case kTcFP16:
         grouped_tc_kernel<kTcFP16><<<grid, kTcThreads, kSmemTotal, stream>>>(kp);
         break;
+    case kTc6xBF16:
+        grouped_tc_kernel<kTc6xBF16><<<grid, kTcThreads, kSmemTotal, stream>>>(kp);
+        break;
     default:
         return cudaErrorInvalidValue;
     }
@@ -48,6 +53,8 @@ int tc_group_cap(int precision)
         return tc_max_group_bytes<kTcTF32>();
     case kTcFP16:
         return tc_max_group_bytes<kTcFP16>();
+    case kTc6xBF16:
+        return tc_max_group_bytes<kTc6xBF16>();
     default:
         return 0;
     }
@@ -62,8 +69,11 @@ void tc_ring(int precision, uint32_t *off, uint32_t *bytes)
     case kTcTF32:
         *off = tc_ring_offset<kTcTF32>(), *bytes = tc_ring_bytes<kTcTF32>();
         break;
-    default:
+    case kTcFP16:
         *off = tc_ring_offset<kTcFP16>(), *bytes = tc_ring_bytes<kTcFP16>();
+        break;
+    default:
+        *off = tc_ring_offset<kTc6xBF16>(), *bytes = tc_ring_bytes<kTc6xBF16>();
         break;
     }
 }

@@ -18,7 +18,8 @@
 //        quarters) -- from the staged FP32
 //        data into the canonical K-major (no swizzle) layout of one of
 //        kTcStages operand stages: X = Xh + Xl (BF16) for 3xBF16,
-//        RN-rounded TF32, or FP16, with zeros past the row's K;
+//        X = Xh + Xm + Xl for 6xBF16, RN-rounded TF32, or FP16, with zeros
+//        past the row's K;
 //   8-15 epilogue: warp 8+e reads quarter e&3 of the accumulator of every
 //        pack whose sequence number is e>>2 modulo kTcEpiPhases, batching two
 //        16-column tensor-memory loads per wait, and writes alpha*acc +
@@ -40,7 +41,7 @@
 
 namespace iaat {
 
-constexpr int kTc3xBF16 = 1, kTcTF32 = 2, kTcFP16 = 3;
+constexpr int kTc3xBF16 = 1, kTcTF32 = 2, kTcFP16 = 3, kTc6xBF16 = 4;
 constexpr int kTcRows = 128;           // MMA M (tensor-memory lanes)
 constexpr int kTcMaxCols = 128;        // columns of one pack (MMA N <= 128)
 constexpr int kTcKC = 32;              // K per operand stage
@@ -67,6 +68,9 @@ template <> struct TcTraits<kTcTF32> {
 };
 template <> struct TcTraits<kTcFP16> {
     static constexpr int kOpBytes = 2, kTerms = 1, kKStep = 16;
+};
+template <> struct TcTraits<kTc6xBF16> {
+    static constexpr int kOpBytes = 2, kTerms = 3, kKStep = 16;
 };
 
 // Canonical K-major layout, no swizzle: core matrices of 8 rows x 16 bytes,
@@ -141,7 +145,7 @@ template <int P>
 __device__ __forceinline__ uint32_t tc_idesc(int n)
 {
     // D = F32; A/B = BF16 (1), F16 (0) or TF32 (2); both K-major; N>>3, M>>4
-    constexpr uint32_t fmt = (P == kTc3xBF16) ? 1u : (P == kTcTF32 ? 2u : 0u);
+    constexpr uint32_t fmt = (P == kTc3xBF16 || P == kTc6xBF16) ? 1u : (P == kTcTF32 ? 2u : 0u);
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
 }
 
@@ -223,9 +227,10 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi)
 }
 
 // Convert one 16-byte core-matrix row (tc_vpr<P>() FP32 values) and store it
-// (hi, and lo for 3xBF16) at byte offset `off` of the term buffers.
+// (hi; lo for 3xBF16; hi, mid, lo for 6xBF16) at byte offset `off` of the
+// term buffers.
 template <int P>
-__device__ __forceinline__ void store_row(char *t0, char *t1, uint32_t off, const float *x)
+__device__ __forceinline__ void store_row(char *t0, char *t1, char *t2, uint32_t off, const float *x)
 {
     if constexpr (P == kTc3xBF16) {
         uint32_t h[4], l[4];
@@ -238,6 +243,23 @@ __device__ __forceinline__ void store_row(char *t0, char *t1, uint32_t off, cons
         }
         *reinterpret_cast<uint4 *>(t0 + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(t1 + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else if constexpr (P == kTc6xBF16) {
+        // each term is the BF16 rounding of what the terms before it leave;
+        // the differences are exact in FP32
+        uint32_t h[4], m[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+            const float r0 = x[2 * q] - __uint_as_float(h[q] << 16);
+            const float r1 = x[2 * q + 1] - __uint_as_float(h[q] & 0xffff0000u);
+            m[q] = pack_bf16(r0, r1);
+            const float s0 = r0 - __uint_as_float(m[q] << 16);
+            const float s1 = r1 - __uint_as_float(m[q] & 0xffff0000u);
+            l[q] = pack_bf16(s0, s1);
+        }
+        *reinterpret_cast<uint4 *>(t0 + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(t1 + off) = make_uint4(m[0], m[1], m[2], m[3]);
+        *reinterpret_cast<uint4 *>(t2 + off) = make_uint4(l[0], l[1], l[2], l[3]);
     } else if constexpr (P == kTcFP16) {
         uint32_t h[4];
 #pragma unroll
@@ -355,6 +377,7 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
                 const int kc = KT > 0 ? min(kTcKC, KT - k0) : 0;
                 char *t0 = T.S.base + kTcOperands + b * tc_stage_bytes<P>() + side * TcTraits<P>::kTerms * OPB;
                 char *t1 = t0 + OPB;
+                char *t2 = t1 + OPB;   // 6xBF16 only
                 if (valid && kc > 0) {
                     const int ng = kc / VPR;
 #pragma unroll 1
@@ -371,7 +394,7 @@ __device__ void tc_converters(const KParams &KP, const TcSmem &T, int cw)
                             for (int e = 0; e < VPR; ++e)
                                 x[e] = (kb + e < myK) ? *reinterpret_cast<const float *>(q + e * sk) : 0.0f;
                         }
-                        store_row<P>(t0, t1, row_off + (uint32_t)(gi * 128), x);
+                        store_row<P>(t0, t1, t2, row_off + (uint32_t)(gi * 128), x);
                     }
                 }
                 if (cw == 0 && lane == 0) {
@@ -453,9 +476,22 @@ __device__ void tc_mma_thread(const KParams &KP, const TcSmem &T, uint32_t tmem)
             // bytes (two core matrices) along K, 16 in the address field
             uint64_t da0 = smem_desc(base, 128, SBO), db0 = smem_desc(base + TcTraits<P>::kTerms * OPB, 128, SBO);
             uint64_t da1 = da0 + (OPB >> 4), db1 = db0 + (OPB >> 4);
+            uint64_t da2 = da1 + (OPB >> 4), db2 = db1 + (OPB >> 4);
             uint32_t accum = (ci.flags & kChunkFirst) ? 0u : 1u;
             for (int ks = 0; ks < ci.kc / KS; ++ks) {
-                if constexpr (P == kTc3xBF16) {
+                if constexpr (P == kTc6xBF16) {
+                    // smallest products first: mm, lh, hl, mh, hm, hh
+                    tc_mma<P>(d, da1, db1, idesc, accum);
+                    tc_mma<P>(d, da2, db0, idesc, 1u);
+                    tc_mma<P>(d, da0, db2, idesc, 1u);
+                    tc_mma<P>(d, da1, db0, idesc, 1u);
+                    tc_mma<P>(d, da0, db1, idesc, 1u);
+                    tc_mma<P>(d, da0, db0, idesc, 1u);
+                    da1 += 16;
+                    db1 += 16;
+                    da2 += 16;
+                    db2 += 16;
+                } else if constexpr (P == kTc3xBF16) {
                     tc_mma<P>(d, da1, db0, idesc, accum);
                     tc_mma<P>(d, da0, db1, idesc, 1u);
                     tc_mma<P>(d, da0, db0, idesc, 1u);

@@ -76,9 +76,9 @@ void apply_text(const std::string &txt, Tuning &t)
 {
     bool a = read_array(txt, "variant_scale_f32", t.scale_f32, kNumVariantsF32);
     bool b = read_array(txt, "variant_scale_f64", t.scale_f64, kNumVariantsF64);
-    for (int i = 0; i < 4; ++i) {
-        static const char *keys[4] = {"group_tasks_ffma", "group_tasks_3xbf16", "group_tasks_tf32",
-                                      "group_tasks_fp16"};
+    for (int i = 0; i < 5; ++i) {
+        static const char *keys[5] = {"group_tasks_ffma", "group_tasks_3xbf16", "group_tasks_tf32",
+                                      "group_tasks_fp16", "group_tasks_6xbf16"};
         if (read_int(txt, keys[i], &t.group_tasks[i], 1, kMaxGroupTasks))
             a = true;
     }
@@ -235,7 +235,7 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
 {
     if (dtype != IAAT_F32 && dtype != IAAT_F64)
         return IAAT_ERR_INVALID_VALUE;
-    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_FP16)
+    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_6XBF16)
         return IAAT_ERR_INVALID_VALUE;
     if (dtype == IAAT_F64 && precision != IAAT_PREC_DEFAULT)
         return IAAT_ERR_UNSUPPORTED;
@@ -359,8 +359,9 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
             std::fprintf(f, "%s%.4f", v ? ", " : "", t.scale_f64[v]);
         std::fprintf(f, "],\n  \"group_tasks_ffma\": %d,\n  \"group_tasks_3xbf16\": %d,\n", t.group_tasks[0],
                      t.group_tasks[1]);
-        std::fprintf(f, "  \"group_tasks_tf32\": %d,\n  \"group_tasks_fp16\": %d,\n  \"group_tasks_dfma\": %d\n}\n",
-                     t.group_tasks[2], t.group_tasks[3], t.group_tasks_f64);
+        std::fprintf(f, "  \"group_tasks_tf32\": %d,\n  \"group_tasks_fp16\": %d,\n  \"group_tasks_6xbf16\": %d,\n",
+                     t.group_tasks[2], t.group_tasks[3], t.group_tasks[4]);
+        std::fprintf(f, "  \"group_tasks_dfma\": %d\n}\n", t.group_tasks_f64);
         std::fclose(f);
     }
     return IAAT_OK;

@@ -13,7 +13,7 @@ struct Tuning {
     double cost_per_slot = 0.5;     // ordering key: bytes per issue slot
     float scale_f32[kNumVariantsF32];
     float scale_f64[kNumVariantsF64];
-    int group_tasks[4] = {0, 0, 0, 0};   // tasks per stage, by iaat_precision_t (0: default)
+    int group_tasks[5] = {0, 0, 0, 0, 0};   // tasks per stage, by iaat_precision_t (0: default)
     int group_tasks_f64 = 0;             // same for FP64 (0: kMaxGroupTasks)
     bool from_cache = false;
     Tuning()

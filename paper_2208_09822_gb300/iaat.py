@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libiaat.so")
 
 IAAT_OP_N, IAAT_OP_T = 0, 1
 IAAT_F32, IAAT_F64 = 0, 1
-IAAT_PREC_DEFAULT, IAAT_PREC_3XBF16, IAAT_PREC_TF32, IAAT_PREC_FP16 = 0, 1, 2, 3
+IAAT_PREC_DEFAULT, IAAT_PREC_3XBF16, IAAT_PREC_TF32, IAAT_PREC_FP16, IAAT_PREC_6XBF16 = 0, 1, 2, 3, 4
 STATUS = {0: "IAAT_OK", 1: "IAAT_ERR_INVALID_VALUE", 2: "IAAT_ERR_NOT_SMALL", 3: "IAAT_ERR_MISALIGNED",
           4: "IAAT_ERR_UNSUPPORTED", 5: "IAAT_ERR_CUDA", 6: "IAAT_ERR_DEVICE_TIMEOUT", 7: "IAAT_ERR_OOM"}
 

@@ -83,10 +83,18 @@ def test_plan_create_rejects_unstageable_k(L, prec, K):
     assert "instance 0" in e.value.message
 
 
-def test_fp64_rejects_tensor_precisions(L):
+@pytest.mark.parametrize("prec", [iaat.IAAT_PREC_3XBF16, iaat.IAAT_PREC_6XBF16])
+def test_fp64_rejects_tensor_precisions(L, prec):
     with pytest.raises(iaat.IaatError) as e:
-        iaat.iaat_plan_create(_desc(), iaat.IAAT_F64, iaat.IAAT_PREC_3XBF16)
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F64, prec)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("prec", [-1, 5])
+def test_unknown_precision_is_rejected(L, prec):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, prec)
+    assert e.value.status == 1
 
 
 def test_single_call_rejects(L):

@@ -28,7 +28,7 @@ def cuda():
 
 
 @pytest.mark.parametrize("prec", [iaat.IAAT_PREC_DEFAULT, iaat.IAAT_PREC_3XBF16, iaat.IAAT_PREC_TF32,
-                                  iaat.IAAT_PREC_FP16])
+                                  iaat.IAAT_PREC_FP16, iaat.IAAT_PREC_6XBF16])
 def test_range_plans_equal_the_whole_plan(cuda, prec):
     torch = cuda
     b = W.uneven(count=20000, seed=21)

@@ -15,7 +15,8 @@ from .gpu_util import compare, padding_untouched, run_grouped, to_device
 
 pytestmark = pytest.mark.gpu
 
-PRECS = {"3xbf16": iaat.IAAT_PREC_3XBF16, "tf32": iaat.IAAT_PREC_TF32, "fp16": iaat.IAAT_PREC_FP16}
+PRECS = {"3xbf16": iaat.IAAT_PREC_3XBF16, "tf32": iaat.IAAT_PREC_TF32, "fp16": iaat.IAAT_PREC_FP16,
+         "6xbf16": iaat.IAAT_PREC_6XBF16}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,6 +52,19 @@ def test_3xbf16_uneven_batch_full():
     assert padding_untouched(b, C)
 
 
+def test_6xbf16_per_instance_accuracy():
+    """The three-term split with six products reaches FP32 accumulation
+    accuracy: the batch within 1e-6 and every instance's guarded error within
+    1e-5, tiny K included (where 3xBF16's dropped Al*Bl term shows most)."""
+    b = W.uneven(count=40000, seed=23)
+    C, info = run_grouped(b, iaat.IAAT_PREC_6XBF16)
+    err = compare(b, C)
+    assert not err["nan"]
+    assert err["eps_batch"] <= 1e-6, err
+    assert err["eps_inst_max"] <= 1e-5, err
+    assert padding_untouched(b, C)
+
+
 @pytest.mark.parametrize("case", ["NN", "NT", "TN", "TT"])
 def test_3xbf16_sweep_every_shape(case):
     b = W.sweep_mixed(case, per_shape=2)
@@ -60,7 +74,7 @@ def test_3xbf16_sweep_every_shape(case):
     assert padding_untouched(b, C)
 
 
-@pytest.mark.parametrize("prec,bound", [("3xbf16", 1e-5), ("tf32", 1e-2), ("fp16", 1e-2)])
+@pytest.mark.parametrize("prec,bound", [("3xbf16", 1e-5), ("tf32", 1e-2), ("fp16", 1e-2), ("6xbf16", 1e-6)])
 def test_precision_study_scaled_entries(prec, bound):
     """The sweep's shapes with every entry of an instance scaled by
     10**U[-3,3]; 3xBF16 must stay within 1e-5, TF32/FP16 are reported."""
