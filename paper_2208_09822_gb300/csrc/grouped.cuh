@@ -432,13 +432,133 @@ __device__ __forceinline__ void repack(T *X, const char *src, int sm, int sk, in
     }
 }
 
+// One k step of the register tile: the lane's MR values of op(A) and NR of
+// op(B) at k, then MR x NR FMAs.  ADIR / BDIR: the operand is read where it
+// was staged (aoff / boff: byte offsets of the lane's rows / columns);
+// otherwise from the warp's canonical chunk buffer, row kk.
+template <typename T, int MR, int NR, int LM, int LN, bool ADIR, bool BDIR>
+__device__ __forceinline__ void k_step(T (&acc)[MR][NR], const char *ak_, const char *bk_, const int (&aoff)[MR],
+                                       const int (&boff)[NR], const T *As, const T *Bs, int kk, int li, int lj)
+{
+    constexpr int ESZ = (int)sizeof(T);
+    constexpr int BM = LM * MR, BN = LN * NR;
+    constexpr int VE = 16 / ESZ;
+    T av[MR], bv[NR];
+    if constexpr (ADIR) {
+#pragma unroll
+        for (int a = 0; a < MR; ++a)
+            av[a] = *reinterpret_cast<const T *>(ak_ + aoff[a]);
+    } else {
+        const T *arow = As + kk * BM;
+        if constexpr (MR >= VE) {
+#pragma unroll
+            for (int q = 0; q < MR / VE; ++q) {
+                const int pos = swz<BM, VE>(li * MR + q * VE, kk);
+                if constexpr (ESZ == 4) {
+                    float4 t4 = *reinterpret_cast<const float4 *>(arow + pos);
+                    av[q * 4 + 0] = t4.x; av[q * 4 + 1] = t4.y;
+                    av[q * 4 + 2] = t4.z; av[q * 4 + 3] = t4.w;
+                } else {
+                    double2 t2 = *reinterpret_cast<const double2 *>(arow + pos);
+                    av[q * 2 + 0] = t2.x; av[q * 2 + 1] = t2.y;
+                }
+            }
+        } else {
+            const int pos = swz<BM, VE>(li * MR, kk);
+#pragma unroll
+            for (int q = 0; q < MR; ++q)
+                av[q] = arow[pos + q];
+        }
+    }
+    if constexpr (BDIR) {
+#pragma unroll
+        for (int b = 0; b < NR; ++b)
+            bv[b] = *reinterpret_cast<const T *>(bk_ + boff[b]);
+    } else {
+        const T *brow = Bs + kk * BN;
+        if constexpr (NR >= VE) {
+#pragma unroll
+            for (int q = 0; q < NR / VE; ++q) {
+                const int pos = swz<BN, VE>(lj * NR + q * VE, kk);
+                if constexpr (ESZ == 4) {
+                    float4 t4 = *reinterpret_cast<const float4 *>(brow + pos);
+                    bv[q * 4 + 0] = t4.x; bv[q * 4 + 1] = t4.y;
+                    bv[q * 4 + 2] = t4.z; bv[q * 4 + 3] = t4.w;
+                } else {
+                    double2 t2 = *reinterpret_cast<const double2 *>(brow + pos);
+                    bv[q * 2 + 0] = t2.x; bv[q * 2 + 1] = t2.y;
+                }
+            }
+        } else {
+            const int pos = swz<BN, VE>(lj * NR, kk);
+#pragma unroll
+            for (int q = 0; q < NR; ++q)
+                bv[q] = brow[pos + q];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < NR; ++b)
+            acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+}
+
+// The block's k-loop, K-chunk by K-chunk: operands not read in place are
+// re-packed into the canonical buffers first, then the k steps run.
+template <typename T, int MR, int NR, int LM, int LN, bool ADIR, bool BDIR>
+__device__ __forceinline__ void k_loop(T (&acc)[MR][NR], const char *Ab, const char *Bb, int am, int ak, int bk,
+                                       int bn, int mh, int nw, int K, const int (&aoff)[MR], const int (&boff)[NR],
+                                       T *As, T *Bs, int li, int lj)
+{
+    constexpr int BM = LM * MR, BN = LN * NR;
+    constexpr int KC = Traits<(int)sizeof(T)>::KC;
+#pragma unroll 1
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const int kc = min(KC, K - k0);
+        const int kcp = (kc + 3) & ~3;
+        if constexpr (!ADIR) {
+            if (am != (int)sizeof(T))
+                repack<T, BM, KC, false>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+            else
+                repack<T, BM, KC, true>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+        }
+        if constexpr (!BDIR) {
+            if (bn == (int)sizeof(T))
+                repack<T, BN, KC, true>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+            else
+                repack<T, BN, KC, false>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+        }
+        if constexpr (!ADIR || !BDIR)
+            __syncwarp();
+        const char *ak_ = Ab + k0 * ak;
+        const char *bk_ = Bb + k0 * bk;
+        // both operands re-packed: their zero padding lets the steps run to
+        // the chunk's K rounded up to 4, four at a time; an operand read in
+        // place has no padding, so then the steps stop at K exactly
+        const int kend = (!ADIR && !BDIR) ? kcp : kc;
+        int kk = 0;
+#pragma unroll 1
+        for (; kk + 4 <= kend; kk += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                k_step<T, MR, NR, LM, LN, ADIR, BDIR>(acc, ak_ + (kk + u) * ak, bk_ + (kk + u) * bk, aoff, boff,
+                                                      As, Bs, kk + u, li, lj);
+        }
+        if constexpr (ADIR || BDIR) {
+#pragma unroll 1
+            for (; kk < kc; ++kk)
+                k_step<T, MR, NR, LM, LN, ADIR, BDIR>(acc, ak_ + kk * ak, bk_ + kk * bk, aoff, boff, As, Bs, kk, li,
+                                                      lj);
+        }
+        if constexpr (!ADIR || !BDIR)
+            __syncwarp();
+    }
+}
+
 template <typename T, int MR, int NR, int LM, int LN>
 __device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, int bi, int bj, T *As, T *Bs)
 {
     constexpr int ESZ = (int)sizeof(T);
-    constexpr int BM = LM * MR, BN = LN * NR;
-    constexpr int KC = Traits<ESZ>::KC;
-    constexpr int VE = 16 / ESZ;
     const int lane = (int)lane_id();
     const int M = r.M, N = r.N, K = r.K;
     const int bh = (M + r.nbm - 1) / r.nbm;
@@ -459,73 +579,102 @@ __device__ __forceinline__ void run_block(const char *smem, const TaskRec &r, in
         const int bk = r.tb ? r.csB : ESZ, bn = r.tb ? ESZ : r.csB;
         const char *Ab = smem + r.offA + r0 * am;
         const char *Bb = smem + r.offB + c0 * bn;
+        // FP64: A not transposed has a lane's MR rows of one column
+        // consecutive in the staged data, B transposed its NR columns of one
+        // row; those operands are read in place (rows / columns past the block
+        // clamped to its last one, their results never stored) instead of
+        // being re-packed (fc64: 9.8 -> 9.1 ms).  FP32 re-packs every operand:
+        // its 16-warp kernel ran slower with the four k-loop versions (the
+        // instruction footprint and register pressure grow).
+        int aoff[MR], boff[NR];
+#pragma unroll
+        for (int a = 0; a < MR; ++a)
+            aoff[a] = min(li * MR + a, mh - 1) * ESZ;
+#pragma unroll
+        for (int b = 0; b < NR; ++b)
+            boff[b] = min(lj * NR + b, nw - 1) * ESZ;
+        if constexpr (ESZ == 4) {
+            constexpr int BM = LM * MR, BN = LN * NR;
+            constexpr int KC = Traits<ESZ>::KC;
+            constexpr int VE = 16 / ESZ;
 #pragma unroll 1
-        for (int k0 = 0; k0 < K; k0 += KC) {
-            const int kc = min(KC, K - k0);
-            const int kcp = (kc + 3) & ~3;
-            if (r.ta)
-                repack<T, BM, KC, false>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
-            else
-                repack<T, BM, KC, true>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
-            if (r.tb)
-                repack<T, BN, KC, true>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
-            else
-                repack<T, BN, KC, false>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
-            __syncwarp();
+            for (int k0 = 0; k0 < K; k0 += KC) {
+                const int kc = min(KC, K - k0);
+                const int kcp = (kc + 3) & ~3;
+                if (r.ta)
+                    repack<T, BM, KC, false>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+                else
+                    repack<T, BM, KC, true>(As, Ab + k0 * ak, am, ak, mh, kc, kcp);
+                if (r.tb)
+                    repack<T, BN, KC, true>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+                else
+                    repack<T, BN, KC, false>(Bs, Bb + k0 * bk, bn, bk, nw, kc, kcp);
+                __syncwarp();
 #pragma unroll 1
-            for (int kk0 = 0; kk0 < kcp; kk0 += 4) {
+                for (int kk0 = 0; kk0 < kcp; kk0 += 4) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int kk = kk0 + u;
-                    const T *arow = As + kk * BM;
-                    const T *brow = Bs + kk * BN;
-                    T av[MR], bv[NR];
-                    if constexpr (MR >= VE) {
+                    for (int u = 0; u < 4; ++u) {
+                        const int kk = kk0 + u;
+                        const T *arow = As + kk * BM;
+                        const T *brow = Bs + kk * BN;
+                        T av[MR], bv[NR];
+                        if constexpr (MR >= VE) {
 #pragma unroll
-                        for (int q = 0; q < MR / VE; ++q) {
-                            const int pos = swz<BM, VE>(li * MR + q * VE, kk);
-                            if constexpr (ESZ == 4) {
-                                float4 t4 = *reinterpret_cast<const float4 *>(arow + pos);
-                                av[q * 4 + 0] = t4.x; av[q * 4 + 1] = t4.y;
-                                av[q * 4 + 2] = t4.z; av[q * 4 + 3] = t4.w;
-                            } else {
-                                double2 t2 = *reinterpret_cast<const double2 *>(arow + pos);
-                                av[q * 2 + 0] = t2.x; av[q * 2 + 1] = t2.y;
+                            for (int q = 0; q < MR / VE; ++q) {
+                                const int pos = swz<BM, VE>(li * MR + q * VE, kk);
+                                if constexpr (ESZ == 4) {
+                                    float4 t4 = *reinterpret_cast<const float4 *>(arow + pos);
+                                    av[q * 4 + 0] = t4.x; av[q * 4 + 1] = t4.y;
+                                    av[q * 4 + 2] = t4.z; av[q * 4 + 3] = t4.w;
+                                } else {
+                                    double2 t2 = *reinterpret_cast<const double2 *>(arow + pos);
+                                    av[q * 2 + 0] = t2.x; av[q * 2 + 1] = t2.y;
+                                }
                             }
+                        } else {
+                            const int pos = swz<BM, VE>(li * MR, kk);
+#pragma unroll
+                            for (int q = 0; q < MR; ++q)
+                                av[q] = arow[pos + q];
                         }
-                    } else {
-                        const int pos = swz<BM, VE>(li * MR, kk);
+                        if constexpr (NR >= VE) {
 #pragma unroll
-                        for (int q = 0; q < MR; ++q)
-                            av[q] = arow[pos + q];
-                    }
-                    if constexpr (NR >= VE) {
-#pragma unroll
-                        for (int q = 0; q < NR / VE; ++q) {
-                            const int pos = swz<BN, VE>(lj * NR + q * VE, kk);
-                            if constexpr (ESZ == 4) {
-                                float4 t4 = *reinterpret_cast<const float4 *>(brow + pos);
-                                bv[q * 4 + 0] = t4.x; bv[q * 4 + 1] = t4.y;
-                                bv[q * 4 + 2] = t4.z; bv[q * 4 + 3] = t4.w;
-                            } else {
-                                double2 t2 = *reinterpret_cast<const double2 *>(brow + pos);
-                                bv[q * 2 + 0] = t2.x; bv[q * 2 + 1] = t2.y;
+                            for (int q = 0; q < NR / VE; ++q) {
+                                const int pos = swz<BN, VE>(lj * NR + q * VE, kk);
+                                if constexpr (ESZ == 4) {
+                                    float4 t4 = *reinterpret_cast<const float4 *>(brow + pos);
+                                    bv[q * 4 + 0] = t4.x; bv[q * 4 + 1] = t4.y;
+                                    bv[q * 4 + 2] = t4.z; bv[q * 4 + 3] = t4.w;
+                                } else {
+                                    double2 t2 = *reinterpret_cast<const double2 *>(brow + pos);
+                                    bv[q * 2 + 0] = t2.x; bv[q * 2 + 1] = t2.y;
+                                }
                             }
+                        } else {
+                            const int pos = swz<BN, VE>(lj * NR, kk);
+#pragma unroll
+                            for (int q = 0; q < NR; ++q)
+                                bv[q] = brow[pos + q];
                         }
-                    } else {
-                        const int pos = swz<BN, VE>(lj * NR, kk);
 #pragma unroll
-                        for (int q = 0; q < NR; ++q)
-                            bv[q] = brow[pos + q];
+                        for (int a = 0; a < MR; ++a)
+#pragma unroll
+                            for (int b = 0; b < NR; ++b)
+                                acc[a][b] = fma(av[a], bv[b], acc[a][b]);
                     }
-#pragma unroll
-                    for (int a = 0; a < MR; ++a)
-#pragma unroll
-                        for (int b = 0; b < NR; ++b)
-                            acc[a][b] = fma(av[a], bv[b], acc[a][b]);
                 }
+                __syncwarp();
             }
-            __syncwarp();
+        } else if (r.ta == 0) {
+            if (r.tb)
+                k_loop<T, MR, NR, LM, LN, true, true>(acc, Ab, Bb, am, ak, bk, bn, mh, nw, K, aoff, boff, As, Bs, li, lj);
+            else
+                k_loop<T, MR, NR, LM, LN, true, false>(acc, Ab, Bb, am, ak, bk, bn, mh, nw, K, aoff, boff, As, Bs, li, lj);
+        } else {
+            if (r.tb)
+                k_loop<T, MR, NR, LM, LN, false, true>(acc, Ab, Bb, am, ak, bk, bn, mh, nw, K, aoff, boff, As, Bs, li, lj);
+            else
+                k_loop<T, MR, NR, LM, LN, false, false>(acc, Ab, Bb, am, ak, bk, bn, mh, nw, K, aoff, boff, As, Bs, li, lj);
         }
     }
 
