@@ -24,7 +24,8 @@
  * rounding back to the storage type happens here.
  *
  * Plant a mistake for the pin tests by compiling with -DORACLE_MUTANT=n
- * (see the switch in oracle_elem); the default build has none.
+ * (1-4: see the switch in oracle_elem; 5-7: oracle_cgemm_batch); the default
+ * build has none.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -139,4 +140,114 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/*
+ * Complex GEMM (CGEMM / ZGEMM; Table I rows 3-4 and the type list of Sec. I,
+ * which name single- and double-precision complex matrix multiplication with
+ * the same four cases NN, NT, TN, TT and no conjugation):
+ *
+ *   C[i,j] = alpha * sum_{k<K} opA(i,k) * opB(k,j) + beta * C0[i,j]
+ *
+ * with complex alpha, beta and entries.  An element is a (real, imaginary)
+ * pair stored next to each other -- 2 floats (is_c64 == 0) or 2 doubles --
+ * and leading dimensions and offsets count elements.  Each complex product
+ * is the textbook one, (a+bi)(c+di) = (ac - bd) + (ad + bc)i: four real
+ * multiplies and four real additions per multiply-add, the 8 flops that
+ * Eq. 2 counts.  Everything is promoted to double and the sum runs k
+ * ascending.  beta == 0 (both parts) means C0 is never read; alpha == 0 (both
+ * parts) or K == 0 skips the sum.  alpha and beta arrive as (re, im) pairs,
+ * already rounded to the instance's component type.  The result of instance
+ * t goes tight (leading dimension M) to Out as (re, im) double pairs starting
+ * at pair offOut[t].
+ *
+ * Planted mistakes (pin tests only): 5 conjugates A, 6 drops the imaginary
+ * part of alpha, 7 flips the sign of beta's imaginary part.
+ */
+static void load_cplx(const void *base, int is_c64, int64_t idx, double *re, double *im)
+{
+    if (is_c64) {
+        *re = ((const double *)base)[2 * idx];
+        *im = ((const double *)base)[2 * idx + 1];
+    } else {
+        *re = (double)((const float *)base)[2 * idx];
+        *im = (double)((const float *)base)[2 * idx + 1];
+    }
+}
+
+int oracle_cgemm_batch(int64_t count, int is_c64,
+                       const int32_t *M, const int32_t *N, const int32_t *K,
+                       const int32_t *lda, const int32_t *ldb,
+                       const int32_t *ldc, const uint8_t *transA,
+                       const uint8_t *transB, const double *alpha,
+                       const double *beta, const void *Apool,
+                       const int64_t *offA, const void *Bpool,
+                       const int64_t *offB, const void *Cpool,
+                       const int64_t *offC, double *Out,
+                       const int64_t *offOut, int nthreads)
+{
+    int64_t t;
+    int bad = 0;
+    size_t esz = is_c64 ? 2 * sizeof(double) : 2 * sizeof(float);
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (t = 0; t < count; ++t)
+        if (M[t] < 0 || N[t] < 0 || K[t] < 0)
+            bad = 1;
+    if (bad)
+        return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (t = 0; t < count; ++t) {
+        const char *A = (const char *)Apool + offA[t] * esz;
+        const char *B = (const char *)Bpool + offB[t] * esz;
+        const char *C0 = (const char *)Cpool + offC[t] * esz;
+        double *o = Out + 2 * offOut[t];
+        double ar = alpha[2 * t], ai = alpha[2 * t + 1];
+        double br = beta[2 * t], bi = beta[2 * t + 1];
+        int i, j, k;
+#if ORACLE_MUTANT == 6
+        ai = 0.0;
+#endif
+#if ORACLE_MUTANT == 7
+        bi = -bi;
+#endif
+        for (j = 0; j < N[t]; ++j) {
+            for (i = 0; i < M[t]; ++i) {
+                double sr = 0.0, si = 0.0, outr, outi;
+                if (ar != 0.0 || ai != 0.0) {
+                    for (k = 0; k < K[t]; ++k) {
+                        int64_t ia = transA[t] ? (int64_t)k + (int64_t)i * lda[t]
+                                               : (int64_t)i + (int64_t)k * lda[t];
+                        int64_t ib = transB[t] ? (int64_t)j + (int64_t)k * ldb[t]
+                                               : (int64_t)k + (int64_t)j * ldb[t];
+                        double xr, xi, yr, yi;
+                        load_cplx(A, is_c64, ia, &xr, &xi);
+                        load_cplx(B, is_c64, ib, &yr, &yi);
+#if ORACLE_MUTANT == 5
+                        xi = -xi;
+#endif
+                        sr += xr * yr - xi * yi;
+                        si += xr * yi + xi * yr;
+                    }
+                }
+                outr = ar * sr - ai * si;
+                outi = ar * si + ai * sr;
+                if (br != 0.0 || bi != 0.0) {
+                    double cr, ci;
+                    load_cplx(C0, is_c64, (int64_t)i + (int64_t)j * ldc[t], &cr, &ci);
+                    outr += br * cr - bi * ci;
+                    outi += br * ci + bi * cr;
+                }
+                o[2 * ((int64_t)i + (int64_t)j * M[t])] = outr;
+                o[2 * ((int64_t)i + (int64_t)j * M[t]) + 1] = outi;
+            }
+        }
+    }
+    return 0;
 }

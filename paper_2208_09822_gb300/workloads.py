@@ -4,7 +4,9 @@ This module draws sizes, transposition cases, leading dimensions, scalars and
 matrix entries; it holds none of the GEMM arithmetic.  The library, its tests,
 the oracle's tests and the benchmark all take their inputs from here.
 
-A batch is stored as three flat pools (A, B, C) of one floating type.  Each
+A batch is stored as three flat pools (A, B, C) of one floating type: real
+(float32 / float64) or complex (complex64 / complex128, the CGEMM and ZGEMM
+types of Table I, an element being a (real, imaginary) pair).  Each
 matrix of instance t starts at an element offset (offA/offB/offC) and is
 stored column-major with its own leading dimension; the stored A is MxK
 (transA == 0) or KxM (transA == 1), the stored B is KxN or NxK, C is MxN.
@@ -82,9 +84,13 @@ class Batch:
             return np.where(tb, N, K), np.where(tb, K, N), self.ldb.astype(np.int64), self.offB
         return M, N, self.ldc.astype(np.int64), self.offC
 
+    @property
+    def is_complex(self):
+        return bool(np.issubdtype(np.dtype(self.dtype), np.complexfloating))
+
     def flops(self):
-        """Eq. 1 numerator: sum of 2*M*N*K."""
-        return int(2 * np.sum(self.M.astype(np.int64) * self.N * self.K))
+        """Eq. 1 numerator, sum of 2*M*N*K; complex types Eq. 2, 8*M*N*K."""
+        return int((8 if self.is_complex else 2) * np.sum(self.M.astype(np.int64) * self.N * self.K))
 
     def algorithmic_bytes(self):
         """Bytes a GEMM must move: A, B, C written, and C read when beta != 0
@@ -171,25 +177,33 @@ def make_batch(M, N, K, ta, tb, alpha, beta, dtype, rng, *, pad=None,
     lda = np.maximum(1, rA + pad[:, 0]); ldb = np.maximum(1, rB + pad[:, 1])
     ldc = np.maximum(1, rC + pad[:, 2])
     esz = np.dtype(dtype).itemsize
+    cplx = bool(np.issubdtype(np.dtype(dtype), np.complexfloating))
     align = max(1, align_bytes // esz)
     mis = [None] * 3 if misalign is None else [np.asarray(misalign)[:, i] for i in range(3)]
     offA, lenA = _layout(rA, cA, lda, align, mis[0])
     offB, lenB = _layout(rB, cB, ldb, align, mis[1])
     offC, lenC = _layout(rC, cC, ldc, align, mis[2])
-    A = np.full(lenA, np.nan, dtype=dtype)
-    B = np.full(lenB, np.nan, dtype=dtype)
-    C = np.full(lenC, C_SENTINEL, dtype=dtype)
+    sent_ab = complex(np.nan, np.nan) if cplx else np.nan
+    sent_c = complex(C_SENTINEL, C_SENTINEL) if cplx else C_SENTINEL
+    A = np.full(lenA, sent_ab, dtype=dtype)
+    B = np.full(lenB, sent_ab, dtype=dtype)
+    C = np.full(lenC, sent_c, dtype=dtype)
     fac = None if scale is None else np.asarray(scale, np.float64)
 
-    def draw(tot, inst):
+    def draw_real(tot):
         if dist == "uniform":
-            v = rng.uniform(-1.0, 1.0, tot)
-        elif dist == "normal":
-            v = rng.standard_normal(tot)
-        elif dist == "int":
-            v = rng.integers(-4, 5, tot).astype(np.float64)
-        else:
-            raise ValueError(dist)
+            return rng.uniform(-1.0, 1.0, tot)
+        if dist == "normal":
+            return rng.standard_normal(tot)
+        if dist == "int":
+            return rng.integers(-4, 5, tot).astype(np.float64)
+        raise ValueError(dist)
+
+    def draw(tot, inst):
+        # complex entries: the real parts of a chunk, then its imaginary parts
+        v = draw_real(tot)
+        if cplx:
+            v = v + 1j * draw_real(tot)
         if fac is not None:
             v = v * fac[inst]
         return v.astype(dtype)
@@ -197,10 +211,11 @@ def make_batch(M, N, K, ta, tb, alpha, beta, dtype, rng, *, pad=None,
     _fill(A, offA, rA, cA, lda, draw)
     _fill(B, offB, rB, cB, ldb, draw)
     _fill(C, offC, rC, cC, ldc, draw)
-    al = np.asarray(alpha, np.float64) * np.ones(n)
-    be = np.asarray(beta, np.float64) * np.ones(n)
-    al = al.astype(dtype).astype(np.float64)
-    be = be.astype(dtype).astype(np.float64)
+    st = np.complex128 if cplx else np.float64
+    al = np.asarray(alpha, st) * np.ones(n, st)
+    be = np.asarray(beta, st) * np.ones(n, st)
+    al = al.astype(dtype).astype(st)
+    be = be.astype(dtype).astype(st)
     i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
     return Batch(dtype, i32(M), i32(N), i32(K), ta, tb, i32(lda), i32(ldb),
                  i32(ldc), al, be, offA, offB, offC, A, B, C, recipe=recipe)
@@ -315,10 +330,40 @@ def fc64(count=100_000, seed=4):
                              f"a=1, b in {{0,1}}, U[-1,1], seed {seed}")
 
 
+def uneven_complex(count=100_000, seed=5, dtype=np.complex64):
+    """The uneven batch in a complex type (CGEMM: complex64, ZGEMM:
+    complex128): M, N, K log-uniform integers on [1, 80] (TN redrawn until
+    MNK <= 32768), case uniform, ld = rows + U{0..7}, alpha and beta with
+    both parts ~ U[-2,2], entries with both parts N(0,1), seed 5."""
+    rng = np.random.default_rng(seed)
+    n = count
+    M = log_uniform_int(rng, 1, 80, n)
+    N = log_uniform_int(rng, 1, 80, n)
+    K = log_uniform_int(rng, 1, 80, n)
+    case = rng.integers(0, 4, n)
+    ta = (case >> 1) & 1
+    tb = case & 1
+    while True:
+        bad = np.nonzero(~in_domain(M, N, K, ta, tb))[0]
+        if len(bad) == 0:
+            break
+        M[bad] = log_uniform_int(rng, 1, 80, len(bad))
+        N[bad] = log_uniform_int(rng, 1, 80, len(bad))
+        K[bad] = log_uniform_int(rng, 1, 80, len(bad))
+    pad = rng.integers(0, 8, (n, 3))
+    alpha = rng.uniform(-2, 2, n) + 1j * rng.uniform(-2, 2, n)
+    beta = rng.uniform(-2, 2, n) + 1j * rng.uniform(-2, 2, n)
+    return make_batch(M, N, K, ta, tb, alpha, beta, dtype, rng, pad=pad,
+                      dist="normal",
+                      recipe=f"uneven-complex: {n} {np.dtype(dtype).name} instances, M,N,K log-U[1,80], "
+                             f"cases uniform, ld=rows+U{{0..7}}, a,b parts ~U[-2,2], N(0,1) parts, seed {seed}")
+
+
 def random_small(count, seed, dtype=np.float32, max_dim=12, pad_max=3,
                  dist="uniform", misalign_max=0, alpha=None, beta=None):
     """Small random instances of every case (tests): dims U{0..max_dim},
-    random ld padding and optional start misalignment."""
+    random ld padding and optional start misalignment.  Complex types draw
+    complex alpha and beta (both parts U[-2,2])."""
     rng = np.random.default_rng(seed)
     n = count
     M = rng.integers(0, max_dim + 1, n)
@@ -329,7 +374,16 @@ def random_small(count, seed, dtype=np.float32, max_dim=12, pad_max=3,
     tb = case & 1
     pad = rng.integers(0, pad_max + 1, (n, 3))
     mis = rng.integers(0, misalign_max + 1, (n, 3)) if misalign_max else None
-    al = rng.uniform(-2, 2, n) if alpha is None else alpha
-    be = rng.uniform(-2, 2, n) if beta is None else beta
+    cplx = np.issubdtype(np.dtype(dtype), np.complexfloating)
+    if alpha is None:
+        al = rng.uniform(-2, 2, n)
+        al = al + 1j * rng.uniform(-2, 2, n) if cplx else al
+    else:
+        al = alpha
+    if beta is None:
+        be = rng.uniform(-2, 2, n)
+        be = be + 1j * rng.uniform(-2, 2, n) if cplx else be
+    else:
+        be = beta
     return make_batch(M, N, K, ta, tb, al, be, dtype, rng, pad=pad, dist=dist,
                       misalign=mis, recipe=f"random_small seed {seed}")
