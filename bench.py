@@ -6,6 +6,7 @@ the end-to-end rate through the C ABI from pinned host memory, and the FP64
 CPU oracle as the reported baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision ffma]
+    python bench.py --workload uneven-c64 ...   # other batches (see WORKLOADS)
     python bench.py --impl reference ...   # the CPU oracle arm
 
 One step = one execution of the whole plan (one persistent kernel launch,
@@ -35,6 +36,31 @@ WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT
 NOMINAL_HBM_GBS = 8000.0
 PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
 
+# Batches bench.py can time.  The default is the uneven FP32 batch (the
+# headline); the others run the CUDA-core path of their type only:
+# name -> (generator, description, default instances, dtype code, path name, tolerance)
+WORKLOADS = {
+    "uneven": ("uneven", WORKLOAD, 200_000, 0, None, 1e-5),
+    "fc64": ("fc64", "fc64-{n}: {n} FP64 instances, M in {{32,64}}, K,N log-uniform int [8,80], NN/TN 50/50 "
+             "(TN redrawn to MNK<=32768), alpha=1, beta in {{0,1}}, U[-1,1], seed 4", 100_000, 1, "dfma", 1e-13),
+    "uneven-c32": ("uneven_complex", "uneven-{n}-c32: {n} complex-float instances (CGEMM), M,N,K log-uniform "
+                   "int [1,80], NN/NT/TN/TT uniform (TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta "
+                   "parts ~U[-2,2], N(0,1) parts, seed 5", 100_000, 2, "cgemm", 1e-5),
+    "uneven-c64": ("uneven_complex", "uneven-{n}-c64: {n} complex-double instances (ZGEMM), M,N,K log-uniform "
+                   "int [1,80], NN/NT/TN/TT uniform (TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta "
+                   "parts ~U[-2,2], N(0,1) parts, seed 5", 100_000, 3, "zgemm", 1e-13),
+}
+DTYPE_NAMES = {0: "f32", 1: "f64", 2: "c32", 3: "c64"}
+
+
+def make_workload(name, n):
+    from paper_2208_09822_gb300 import workloads as W
+    gen, _, default_n, code, _, _ = WORKLOADS[name]
+    n = default_n if n is None else n
+    if gen == "uneven_complex":
+        return W.uneven_complex(count=n, dtype=np.complex64 if code == 2 else np.complex128)
+    return getattr(W, gen)(count=n)
+
 
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
@@ -58,10 +84,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic(precision):
+def profile_traffic(precision, workload="uneven", count=200_000):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"grouped_{precision}_uneven200k.md")
+    path = os.path.join(ROOT, "profiles", f"grouped_{precision}_{workload}{count // 1000}k.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -134,18 +160,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_baseline_leg(batch, gpu_results, min_seconds):
+def cpu_baseline_leg(batch, gpu_results, min_seconds, tol=1e-5):
     """The CPU-baseline leg: time the FP64 oracle over the whole batch
     (repeated until min_seconds), and use its result to measure the error of
     each path's first launch."""
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from gpu_util import errors
+    run = oracle.cgemm_batch if batch.is_complex else oracle.gemm_batch
     flops = batch.flops()
     t0 = time.perf_counter()
     reps = 0
     while True:
-        ref, _ = oracle.gemm_batch(batch)
+        ref, _ = run(batch)
         reps += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
@@ -156,7 +183,7 @@ def cpu_baseline_leg(batch, gpu_results, min_seconds):
     for name, res in gpu_results.items():
         e = errors(batch, res, ref)
         errs[name] = {k: e[k] for k in ("eps_batch", "eps_inst_max", "eps_inst_median", "eps_inst_rms")}
-        errs[name]["within_1e-5"] = e["eps_batch"] <= 1e-5
+        errs[name][f"within_{tol:g}"] = e["eps_batch"] <= tol
     return cpu, errs
 
 
@@ -166,16 +193,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    from paper_2208_09822_gb300 import workloads as W
-    batch = W.uneven()
+    batch = make_workload(args.workload, args.instances)
+    run = oracle.cgemm_batch if batch.is_complex else oracle.gemm_batch
     # one step = the oracle over a bounded sample of the batch (every 8th instance)
     sample = batch.select(np.arange(0, batch.count, 8))
     flops = sample.flops()
     for _ in range(args.warmup):
-        oracle.gemm_batch(sample)
+        run(sample)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.gemm_batch(sample)
+        run(sample)
     dt = time.perf_counter() - t0
     value = flops * args.steps / dt / 1e9
     cores = oracle.max_threads()
@@ -184,7 +211,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.format(n=batch.count), "sample": f"every 8th instance ({sample.count} instances, "
+        "config": {"workload": WORKLOADS[args.workload][1].format(n=batch.count),
+                   "sample": f"every 8th instance ({sample.count} instances, "
                                                    f"{flops / 1e9:.3f} GFLOP) per step"},
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"every 8th instance of the batch ({sample.count}), FP64 triple loop"},
@@ -209,8 +237,11 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="instance ranges the end-to-end leg pipelines copies and launches over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--instances", type=int, default=200_000,
-                    help="instances of the uneven batch (smaller only for profiling captures)")
+    ap.add_argument("--workload", default="uneven", choices=sorted(WORKLOADS),
+                    help="the batch: uneven FP32 (the headline; --precision and --compare apply), or one "
+                         "timed on its CUDA-core path only (fc64, uneven-c32 = CGEMM, uneven-c64 = ZGEMM)")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="instances of the batch (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the built-in cost model instead of tuning each path first")
     args = ap.parse_args()
@@ -238,27 +269,50 @@ def main():
     # the autotuner (Sec. IV's install-time tuning, done at start-up here):
     # per-variant costs and the stage size of every timed path, measured on
     # this GPU before anything is timed; skipped when a tuning cache is given
+    _, wl_desc, _, wl_dtype, wl_path, wl_tol = WORKLOADS[args.workload]
+    if args.workload != "uneven":
+        # other batches: their type's CUDA-core path alone
+        args.precision = wl_path
+        args.compare = []
+
     tuned = "built-in cost model"
-    if not args.no_autotune and not os.environ.get("IAAT_TUNE_CACHE"):
+    if not args.no_autotune and not os.environ.get("IAAT_TUNE_CACHE") and wl_dtype in (0, 1):
         t0 = time.time()
-        for name in dict.fromkeys([args.precision] + list(args.compare)):
-            iaat.iaat_autotune(iaat.IAAT_F32, PRECISIONS[name], None)
+        if wl_dtype == 0:
+            for name in dict.fromkeys([args.precision] + list(args.compare)):
+                iaat.iaat_autotune(iaat.IAAT_F32, PRECISIONS[name], None)
+        else:
+            iaat.iaat_autotune(iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT, None)
         tuned = f"autotuned at start-up ({time.time() - t0:.1f} s, outside the timed region)"
     elif os.environ.get("IAAT_TUNE_CACHE"):
         tuned = "tuning cache " + os.environ["IAAT_TUNE_CACHE"]
+    elif wl_dtype in (2, 3):
+        tuned = "built-in cost model (the complex family is not autotuned)"
 
-    batch = W.uneven(count=args.instances)
+    batch = make_workload(args.workload, args.instances)
     tA = torch.from_numpy(batch.A).to(dev)
     tB = torch.from_numpy(batch.B).to(dev)
     tC = torch.from_numpy(batch.C).to(dev)
     C0 = tC.clone()
-    descs = iaat.descs_for_pools(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+    to_descs = iaat.cdescs_for_pools if batch.is_complex else iaat.descs_for_pools
+    descs = to_descs(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
     stream = torch.cuda.Stream(device=dev)
+
+    def make_plan(d, name):
+        if wl_dtype == 0:
+            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name])
+        if wl_dtype == 1:
+            return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
+        return iaat.iaat_plan_create_complex(d, wl_dtype)
+
+    # the DFMA-bound batches are held against the measured DFMA rate
+    dfma_bound = wl_dtype in (1, 3)
+    dfma_peak = iaat.iaat_fma_peak(iaat.IAAT_F64) if dfma_bound else None
 
     def time_path(name):
         """First launch (kept for the error check), then a CUDA graph of one
         launch replayed `steps` times between events on the launch stream."""
-        plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, PRECISIONS[name])
+        plan = make_plan(descs, name)
         info = iaat.iaat_plan_info(plan)
         tC.copy_(C0)
         torch.cuda.synchronize()
@@ -359,7 +413,7 @@ def main():
         parts = []
         for b0, b1 in ranges:
             span = lambda off, pool: (int(off[b0]), int(off[b1]) if b1 < n else pool.size)
-            parts.append((iaat.iaat_plan_create(descs[b0:b1], iaat.IAAT_F32, PRECISIONS[args.precision]),
+            parts.append((make_plan(descs[b0:b1], args.precision),
                           span(batch.offA, batch.A), span(batch.offB, batch.B), span(batch.offC, batch.C)))
         s_in = torch.cuda.Stream(device=dev)
         s_out = torch.cuda.Stream(device=dev)
@@ -420,31 +474,39 @@ def main():
     if rank == 0:
         cpu, errs = None, {}
         if world == 1 and not args.no_cpu_baseline:
-            cpu, errs = cpu_baseline_leg(batch, {k: v[2] for k, v in results.items()}, 10.0)
-        traffic = profile_traffic(args.precision)
+            cpu, errs = cpu_baseline_leg(batch, {k: v[2] for k, v in results.items()}, 10.0, wl_tol)
+        traffic = profile_traffic(args.precision, args.workload, batch.count)
         paths = {}
         for name, (inf, ms_p, _) in results.items():
             paths[name] = {"value": inf["flops"] * world / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
                            "ms_per_step": ms_p,
                            "roofline_frac": inf["algorithmic_bytes"] / (ms_p * 1e-3) / 1e9 / peaks["hbm_gbs"],
                            "error": errs.get(name)}
+        if dfma_bound:
+            roofline = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": dfma_peak / 1e3,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e9 / dfma_peak, "traffic": traffic,
+                        "peak_kind": "measured DFMA rate (iaat_fma_peak, this GPU, at start-up)",
+                        "algorithmic_bytes_per_launch": abytes,
+                        "hbm_frac": achieved / peaks["hbm_gbs"]}
+        else:
+            roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                        "peak_kind": f"{peak_kind} copy bandwidth",
+                        "algorithmic_bytes_per_launch": abytes,
+                        "roofline_gflops_at_8TBs": roof_gflops,
+                        "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None}
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(n=batch.count), "instances": batch.count,
+            "vs_baseline": None, "dtype": DTYPE_NAMES[wl_dtype], "data": "synthetic",
+            "config": {"workload": wl_desc.format(n=batch.count), "instances": batch.count,
                        "precision": args.precision,
                        "parallelism": f"instances x{world} (one batch per GPU)",
                        "l2": "inputs larger than L2 (pools %.2f GB > 129 MB); no flush" %
                              ((batch.A.nbytes + batch.B.nbytes + batch.C.nbytes) / 1e9),
                        "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
                        "grid": info["grid"], "tuning": tuned},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "peak_kind": f"{peak_kind} copy bandwidth",
-                         "algorithmic_bytes_per_launch": abytes,
-                         "roofline_gflops_at_8TBs": roof_gflops,
-                         "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,

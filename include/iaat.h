@@ -19,8 +19,9 @@
  *   ldc >= max(1, M).  M == 0 or N == 0: nothing is done.  alpha == 0 or
  *   K == 0: C = beta * C and A, B are not read.  beta == 0: C is not read, so
  *   NaN or Inf already in C does not reach the result.  Elements of C outside
- *   its M x N part (the ld padding) are never written.  FP32 pointers must be
- *   4-byte aligned and FP64 pointers 8-byte aligned (IAAT_ERR_MISALIGNED).
+ *   its M x N part (the ld padding) are never written.  Pointers must be
+ *   aligned to the element size: 4 bytes (FP32), 8 (FP64 and complex float),
+ *   16 (complex double); otherwise IAAT_ERR_MISALIGNED.
  *   A, B and C of one call or one plan must not overlap in written memory.
  *
  * Memory and execution:
@@ -47,7 +48,11 @@ extern "C" {
 
 typedef enum { IAAT_OP_N = 0, IAAT_OP_T = 1 } iaat_op_t;
 
-typedef enum { IAAT_F32 = 0, IAAT_F64 = 1 } iaat_dtype_t;
+/* Element types.  IAAT_C32 / IAAT_C64 are the complex types of Table I
+ * (CGEMM / ZGEMM): an element is a (real, imaginary) pair stored next to each
+ * other, 2 floats (8 bytes) or 2 doubles (16 bytes); leading dimensions count
+ * elements.  Complex batches are planned with iaat_plan_create_complex. */
+typedef enum { IAAT_F32 = 0, IAAT_F64 = 1, IAAT_C32 = 2, IAAT_C64 = 3 } iaat_dtype_t;
 
 /* Arithmetic used for an FP32 plan (FP64 plans accept only the default).
  * DEFAULT: FP32 FFMA on the CUDA cores (FP64: DFMA).
@@ -90,6 +95,25 @@ typedef struct {
     void *C;
 } iaat_gemm_desc_t;
 
+/* One complex GEMM instance (CGEMM / ZGEMM, Table I rows 3-4):
+ *   C = alpha * op(A) * op(B) + beta * C  with complex alpha, beta, A, B, C,
+ * op = N or T as above (the paper's four cases; no conjugate transpose).
+ * Same sizes, leading dimensions, domain and argument rules as the real
+ * GEMM; alpha == 0 and beta == 0 mean both parts zero.  alpha and beta are
+ * rounded to the component type of the plan.  Each complex multiply-add is
+ * four real multiply-adds on the FP32 / FP64 pipes, so a plan's flops count
+ * 8*M*N*K per instance (Eq. 2). */
+typedef struct {
+    int32_t M, N, K;
+    int32_t lda, ldb, ldc;
+    int32_t transA, transB;
+    double alpha_re, alpha_im;
+    double beta_re, beta_im;
+    const void *A;
+    const void *B;
+    void *C;
+} iaat_cgemm_desc_t;
+
 typedef struct iaat_plan_s *iaat_plan_t;
 
 /* Optional knobs of iaat_plan_create (pass NULL for the tuned defaults).
@@ -111,7 +135,8 @@ typedef struct {
     int64_t tasks;             /* work pieces after splitting */
     int64_t groups;            /* pipeline stages */
     int64_t blocks;            /* warp blocks over all tasks (tensor-core plans: MMA packs) */
-    int64_t flops;             /* sum of 2*M*N*K over active instances (Eq. 1) */
+    int64_t flops;             /* sum of 2*M*N*K over active instances (Eq. 1);
+                                  complex plans 8*M*N*K (Eq. 2) */
     int64_t algorithmic_bytes; /* A, B, C written, C read when beta != 0 */
     int64_t plan_bytes;        /* device bytes the plan holds (descriptors) */
     int32_t grid;              /* CTAs of each launch */
@@ -164,11 +189,25 @@ iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t c
  * Sec. V-A), groups the pieces into pipeline stages, orders them for the
  * persistent schedule and copies the descriptors to the device (synchronous;
  * uses the current CUDA device).  The plan keeps the pointers: re-plan when
- * they change.  `opts` may be NULL. */
+ * they change.  `opts` may be NULL.  dtype IAAT_F32 or IAAT_F64 (complex
+ * dtypes: iaat_plan_create_complex; here IAAT_ERR_INVALID_VALUE). */
 iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t count,
                                iaat_dtype_t dtype, iaat_precision_t precision,
                                const iaat_plan_options_t *opts,
                                iaat_plan_t *out);
+
+/* Build a plan for `count` complex instances, dtype IAAT_C32 (CGEMM) or
+ * IAAT_C64 (ZGEMM): the same validation, tiling into warp blocks of the
+ * complex register-tile family, stage programs and persistent schedule as
+ * iaat_plan_create (which refuses complex dtypes), plus a device table of
+ * each instance's alpha and beta that the plan owns.  The complex kernel runs
+ * on the CUDA cores (FFMA / DFMA) only.  Run it with iaat_gemm_grouped;
+ * check, inspect and free it like any plan.  `opts` may be NULL (its
+ * force_variant picks from the complex family, 1..5). */
+iaat_status_t iaat_plan_create_complex(const iaat_cgemm_desc_t *descs, int64_t count,
+                                       iaat_dtype_t dtype,
+                                       const iaat_plan_options_t *opts,
+                                       iaat_plan_t *out);
 
 /* Enqueue one execution of the plan (the kernel executing plan, Sec. V-B) on
  * `stream`: one persistent kernel launch, no host synchronisation and no
@@ -198,8 +237,9 @@ iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops);
 
 /* Host-only view of the run-time tiler (no GPU needed).  Tiles one M x N
  * (x K) instance of the given type and case with the library's register-tile
- * variants and writes up to `cap` blocks as (row0, col0, rows, cols)
- * quadruples to `blocks`.  Returns the number of blocks (may exceed `cap`),
+ * variants (all four dtypes; complex ones with the complex family) and
+ * writes up to `cap` blocks as (row0, col0, rows, cols) quadruples to
+ * `blocks`.  Returns the number of blocks (may exceed `cap`),
  * or -1 on bad arguments. */
 int64_t iaat_tile(iaat_dtype_t dtype, int transA, int transB, int M, int N,
                   int K, int32_t *blocks, int64_t cap);

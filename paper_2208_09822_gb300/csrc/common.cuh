@@ -47,9 +47,13 @@ constexpr uint8_t kFlagReadC = 1;
 
 // alpha or beta of a task record, in the plan's precision: FP64 plans read
 // the double, FP32 plans the float (no FP64 conversion on the device).
+// Complex plans keep alpha and beta in a table of the plan; the record's
+// alpha then holds the address of the instance's entry (re(alpha),
+// im(alpha), re(beta), im(beta) in the component type).
 union RecScalar {
     double d;
     float f;
+    const void *p;
 };
 
 // What the consumer warps see of a task once its operands sit in shared
@@ -199,6 +203,26 @@ constexpr Variant kVariantsF64[kNumVariantsF64] = {
     {1, 2, 8, 4},   // 4: 8 x 8
 };
 
+// Complex families (CGEMM / ZGEMM, Table I rows 3-4): an accumulator is a
+// (re, im) pair, so a complex-float tile takes the registers of an FP64 tile
+// of the same shape and a complex-double tile twice that; the complex-double
+// tiles are half the size.
+constexpr int kNumVariantsC = 5;
+constexpr Variant kVariantsC32[kNumVariantsC] = {
+    {4, 8, 8, 4},   // 0: 32 x 32
+    {4, 4, 8, 4},   // 1: 32 x 16
+    {4, 4, 4, 8},   // 2: 16 x 32
+    {2, 4, 8, 4},   // 3: 16 x 16
+    {1, 2, 8, 4},   // 4: 8 x 8
+};
+constexpr Variant kVariantsC64[kNumVariantsC] = {
+    {4, 4, 8, 4},   // 0: 32 x 16
+    {4, 4, 4, 8},   // 1: 16 x 32
+    {2, 4, 8, 4},   // 2: 16 x 16
+    {2, 2, 8, 4},   // 3: 16 x 8
+    {1, 2, 8, 4},   // 4: 8 x 8
+};
+
 // K is consumed in chunks of kKC (FP32) / kKC64 (FP64) staged per warp.
 constexpr int kKC = 16;
 constexpr int kKC64 = 8;
@@ -234,6 +258,13 @@ constexpr int kSmemTotal = 227 * 1024;
 template <int ESZ> IAAT_CE int ring_bytes() { return (kSmemTotal - smem_ring_offset<ESZ>()) & ~127; }
 // A stage may take at most half the ring, so two always fit.
 template <int ESZ> IAAT_CE int max_group_bytes() { return ring_bytes<ESZ>() / 2; }
+
+// Complex kernel: kCplxWarps consumer warps that read the staged operands in
+// place (no per-warp buffers), so its ring starts right after the slots.
+constexpr int kCplxWarps = 8;
+IAAT_CE int cplx_ring_offset() { return (kSmemCanon + 127) & ~127; }
+IAAT_CE int cplx_ring_bytes() { return (kSmemTotal - cplx_ring_offset()) & ~127; }
+IAAT_CE int cplx_max_group_bytes() { return cplx_ring_bytes() / 2; }
 
 // Order in which the CTAs take the cost-sorted stages: stage i of CTA `cta`
 // is group sched_group(i, cta, ncta), a snake over the groups that balances

@@ -77,14 +77,25 @@ static iaat_status_t check_instance(int64_t idx, int M, int N, int K, int lda, i
 // the FMAs and tile loads of the k-loop, the re-pack of each K-chunk (the
 // memops term of Sec. V-A: m_i + n_i values per k), and a fixed epilogue.
 
-static const Variant *variants(int esz, int *n)
+static bool is_complex(int dt) { return dt == IAAT_C32 || dt == IAAT_C64; }
+static int dtype_esz(int dt) { return dt == IAAT_F32 ? 4 : (dt == IAAT_C64 ? 16 : 8); }
+
+static const Variant *variants(int dt, int *n)
 {
-    if (esz == 4) {
+    switch (dt) {
+    case IAAT_F32:
         *n = kNumVariantsF32;
         return kVariantsF32;
+    case IAAT_C32:
+        *n = kNumVariantsC;
+        return kVariantsC32;
+    case IAAT_C64:
+        *n = kNumVariantsC;
+        return kVariantsC64;
+    default:
+        *n = kNumVariantsF64;
+        return kVariantsF64;
     }
-    *n = kNumVariantsF64;
-    return kVariantsF64;
 }
 
 namespace iaat {
@@ -93,7 +104,16 @@ namespace iaat {
 double model_block_cost(const Variant &v, int esz, int K);
 }
 
-static double block_cost(const Variant &v, int esz, int K) { return iaat::model_block_cost(v, esz, K); }
+// Complex tiles read the staged operands in place: per k term MR + NR
+// element loads and 4*MR*NR FMAs (Eq. 2's four real products per complex
+// one; DFMA-weighted for complex double), then a complex epilogue.
+static double block_cost(const Variant &v, int dt, int K)
+{
+    if (!is_complex(dt))
+        return iaat::model_block_cost(v, dtype_esz(dt), K);
+    const double fma = 4.0 * v.mr * v.nr * (dt == IAAT_C64 ? tuning().dfma_weight : 1.0);
+    return (double)K * (fma + v.mr + v.nr) + 2.0 * tuning().epilogue_weight * v.mr * v.nr + tuning().block_overhead;
+}
 
 double iaat::model_block_cost(const Variant &v, int esz, int K)
 {
@@ -117,10 +137,11 @@ struct TileChoice {
 // CUDA-core kernel); the tensor-core planner only uses the cost as an
 // ordering key and takes the plain model, so that tuning the CUDA-core
 // kernel does not reorder tensor-core stages.
-static TileChoice choose_tiling(int esz, int M, int N, int K, int force_variant, bool scaled = true)
+static TileChoice choose_tiling(int dt, int M, int N, int K, int force_variant, bool scaled = true)
 {
     int nv;
-    const Variant *vs = variants(esz, &nv);
+    const Variant *vs = variants(dt, &nv);
+    scaled = scaled && !is_complex(dt);   // the autotuner calibrates the real families
     TileChoice best{0, 1, 1, 1e300};
     for (int v = 0; v < nv; ++v) {
         if (force_variant >= 0 && v != force_variant)
@@ -129,7 +150,8 @@ static TileChoice choose_tiling(int esz, int M, int N, int K, int force_variant,
         const int nbm = std::max(1, (M + bm - 1) / bm), nbn = std::max(1, (N + bn - 1) / bn);
         if (nbm > 255 || nbn > 255)
             continue;
-        const double c = (double)nbm * nbn * block_cost(vs[v], esz, K) * (scaled ? tuning().variant_scale(esz, v) : 1.0);
+        const double c =
+            (double)nbm * nbn * block_cost(vs[v], dt, K) * (scaled ? tuning().variant_scale(dtype_esz(dt), v) : 1.0);
         if (c < best.cost)
             best = TileChoice{v, nbm, nbn, c};
     }
@@ -141,12 +163,11 @@ extern "C" int64_t iaat_tile(iaat_dtype_t dtype, int transA, int transB, int M, 
 {
     (void)transA;
     (void)transB;
-    if ((dtype != IAAT_F32 && dtype != IAAT_F64) || M < 0 || N < 0 || K < 0 || cap < 0 || (cap > 0 && !blocks))
+    if (dtype < IAAT_F32 || dtype > IAAT_C64 || M < 0 || N < 0 || K < 0 || cap < 0 || (cap > 0 && !blocks))
         return -1;
     if (M == 0 || N == 0)
         return 0;
-    const int esz = dtype == IAAT_F32 ? 4 : 8;
-    const TileChoice t = choose_tiling(esz, M, N, K, -1);
+    const TileChoice t = choose_tiling(dtype, M, N, K, -1);
     const int bh = (M + t.nbm - 1) / t.nbm, bw = (N + t.nbn - 1) / t.nbn;
     int64_t n = 0;
     for (int bj = 0; bj < t.nbn; ++bj)
@@ -235,6 +256,7 @@ struct iaat_plan_s {
     char *d_prog = nullptr;        // stage programs
     int64_t *d_poff = nullptr;     // program offset per group
     int32_t *d_err = nullptr;
+    char *d_scal = nullptr;        // complex plans: alpha, beta of every instance
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
     iaat_plan_info_t info{};
@@ -249,16 +271,19 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][6];
+bool g_prepared[64][8];
 
-// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2..5 = tcgen05 precision (kind - 1)
+// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2..5 = tcgen05 precision (kind - 1),
+// 6 = complex float, 7 = complex double
 iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
     if (dev < 0 || dev >= 64)
         return fail(IAAT_ERR_CUDA, "device index %d out of range", dev);
     if (!g_prepared[dev][kind]) {
-        cudaError_t e = kind < 2 ? prepare_fma(kind) : prepare_tc(kind - 1);
+        cudaError_t e = kind < 2   ? prepare_fma(kind)
+                        : kind < 6 ? prepare_tc(kind - 1)
+                                   : prepare_cplx(kind == 6 ? IAAT_C32 : IAAT_C64);
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaFuncSetAttribute");
         g_prepared[dev][kind] = true;
@@ -266,7 +291,12 @@ iaat_status_t prepare_device(int dev, int kind)
     return IAAT_OK;
 }
 
-int kernel_kind(int esz, iaat_precision_t prec) { return prec != IAAT_PREC_DEFAULT ? 1 + (int)prec : (esz == 4 ? 0 : 1); }
+int kernel_kind(int dt, iaat_precision_t prec)
+{
+    if (is_complex(dt))
+        return dt == IAAT_C32 ? 6 : 7;
+    return prec != IAAT_PREC_DEFAULT ? 1 + (int)prec : (dt == IAAT_F32 ? 0 : 1);
+}
 
 int g_sm_count[64];
 
@@ -363,9 +393,14 @@ bool choose_split(const iaat_gemm_desc_t &g, int esz, int Keff, uint32_t cap, in
 // Build the tasks of one instance: one, or its pieces.  piece > 0: cut C into
 // pieces of at most piece x piece as well (the single-call path spreads one
 // instance over several SMs that way).
-iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool tc, int force_variant, uint32_t cap,
+// Complex plans (dt IAAT_C32 / IAAT_C64): g carries alpha and beta only as
+// markers (alpha 0 or 1; beta 0, 1 or 2 for "other"), and each task's alpha
+// field holds the instance index, which build_programs turns into the address
+// of the instance's entry in the plan's scalar table.
+iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc, int force_variant, uint32_t cap,
                          std::vector<HostTask> &out, int64_t *blocks_out, int piece = 0)
 {
+    const int esz = dtype_esz(dt);
     const int M = g.M, N = g.N;
     if (M == 0 || N == 0)
         return IAAT_OK;
@@ -385,7 +420,11 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int esz, bool t
             int c0, w;
             piece_range(N, pn, j, c0, w);
             TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
-            const TileChoice t = choose_tiling(esz, h, w, Keff, force_variant, !tc);
+            if (is_complex(dt)) {
+                d.alpha = (double)idx;
+                d.beta = 0.0;
+            }
+            const TileChoice t = choose_tiling(dt, h, w, Keff, force_variant, !tc);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
             d.nbn = (uint8_t)t.nbn;
@@ -504,8 +543,8 @@ void emit_copies(const Stage &st, const char *p, int h, int w, int ld, int esz, 
 
 iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vector<int32_t> &gbeg,
                              const std::vector<PackInfo> &packs, const std::vector<int32_t> &pbeg, int esz, bool tc,
-                             int grid, uint32_t ring_off, uint32_t ring_bytes, std::vector<char> &prog,
-                             std::vector<int64_t> &poff)
+                             int grid, uint32_t ring_off, uint32_t ring_bytes, const char *scal, uint32_t scal_stride,
+                             std::vector<char> &prog, std::vector<int64_t> &poff)
 {
     const int ng = (int)gbeg.size() - 1;
     poff.assign((size_t)std::max(ng, 1), 0);
@@ -573,7 +612,10 @@ iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vecto
                 r.M = d.M; r.N = d.N; r.K = d.K;
                 r.ta = d.ta; r.tb = d.tb; r.variant = d.variant; r.flags = d.flags;
                 r.nbm = d.nbm; r.nbn = d.nbn;
-                set_scalars(r, d.alpha, d.beta, esz);
+                if (scal)   // complex plan: the instance's scalar-table entry
+                    r.alpha.p = scal + (int64_t)d.alpha * scal_stride;
+                else
+                    set_scalars(r, d.alpha, d.beta, esz);
                 nbi += (int)d.nbm * (int)d.nbn;
                 hd.prefix[t] = nbi;
                 tx[t] = s.a.tx + s.b.tx + (tc ? 0u : s.c.tx);
@@ -620,28 +662,23 @@ iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vecto
 
 }  // namespace
 
-extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t count, iaat_dtype_t dtype,
-                                          iaat_precision_t precision, const iaat_plan_options_t *opts,
-                                          iaat_plan_t *out)
+// The planner behind iaat_plan_create and iaat_plan_create_complex.  cscal:
+// complex plans only, (re alpha, im alpha, re beta, im beta) per instance,
+// already rounded to the component type; the descriptors then carry alpha
+// and beta as markers (see make_tasks).
+static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t count, int dt,
+                                      iaat_precision_t precision, const iaat_plan_options_t *opts,
+                                      const double *cscal, iaat_plan_t *out)
 {
-    if (!out)
-        return fail(IAAT_ERR_INVALID_VALUE, "out is NULL");
-    *out = nullptr;
-    if (count < 0 || (count > 0 && !descs))
-        return fail(IAAT_ERR_INVALID_VALUE, "bad descriptor array");
-    if (dtype != IAAT_F32 && dtype != IAAT_F64)
-        return fail(IAAT_ERR_INVALID_VALUE, "unknown dtype %d", (int)dtype);
-    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_6XBF16)
-        return fail(IAAT_ERR_INVALID_VALUE, "unknown precision %d", (int)precision);
-    if (precision != IAAT_PREC_DEFAULT && dtype == IAAT_F64)
-        return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");
-    const int esz = dtype == IAAT_F32 ? 4 : 8;
+    const int esz = dtype_esz(dt);
     const bool tc = precision != IAAT_PREC_DEFAULT;
-    const uint32_t cap = tc ? (uint32_t)tc_group_cap((int)precision)
-                            : (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
+    const bool cplx = is_complex(dt);
+    const uint32_t cap = tc     ? (uint32_t)tc_group_cap((int)precision)
+                         : cplx ? (uint32_t)cplx_max_group_bytes()
+                                : (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>());
     int max_tasks = kMaxGroupTasks;
-    {
-        const int tuned = dtype == IAAT_F64 ? tuning().group_tasks_f64 : tuning().group_tasks[(int)precision];
+    if (!cplx) {
+        const int tuned = dt == IAAT_F64 ? tuning().group_tasks_f64 : tuning().group_tasks[(int)precision];
         if (tuned > 0)
             max_tasks = tuned;
     }
@@ -652,7 +689,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
             max_tasks = std::min(opts->max_group_tasks, kMaxGroupTasks);
         if (opts->force_variant > 0) {
             int nv;
-            variants(esz, &nv);
+            variants(dt, &nv);
             if (opts->force_variant > nv)
                 return fail(IAAT_ERR_INVALID_VALUE, "force_variant %d out of range", opts->force_variant);
             force_variant = opts->force_variant - 1;
@@ -666,7 +703,7 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     tasks.reserve((size_t)count);
     iaat_plan_info_t info{};
     info.instances = count;
-    info.dtype = dtype;
+    info.dtype = dt;
     info.precision = precision;
     int64_t nblocks = 0;
     for (int64_t i = 0; i < count; ++i) {
@@ -676,13 +713,13 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         if (st != IAAT_OK)
             return st;
         const size_t before = tasks.size();
-        st = make_tasks(i, g, esz, tc, force_variant, cap, tasks, &nblocks);
+        st = make_tasks(i, g, dt, tc, force_variant, cap, tasks, &nblocks);
         if (st != IAAT_OK)
             return st;
         if (tasks.size() > before) {
             info.active += 1;
             const int64_t M = g.M, N = g.N, K = (g.alpha == 0.0) ? 0 : g.K;
-            info.flops += 2 * M * N * g.K * (g.alpha == 0.0 ? 0 : 1);
+            info.flops += (cplx ? 8 : 2) * M * N * g.K * (g.alpha == 0.0 ? 0 : 1);
             info.algorithmic_bytes += (M * K + K * N + M * N + (g.beta != 0.0 ? M * N : 0)) * esz;
         }
     }
@@ -704,13 +741,13 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         delete plan;
         return cuda_fail(e, "cudaGetDevice");
     }
-    iaat_status_t ps = prepare_device(plan->device, kernel_kind(esz, precision));
+    iaat_status_t ps = prepare_device(plan->device, kernel_kind(dt, precision));
     if (ps != IAAT_OK) {
         delete plan;
         return ps;
     }
     plan->esz = esz;
-    plan->dtype = dtype;
+    plan->dtype = (iaat_dtype_t)dt;
     plan->precision = precision;
     plan->ntasks = (int64_t)flat.size();
     plan->ngroups = (int64_t)gbeg.size() - 1;
@@ -719,13 +756,42 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     uint32_t ring_off = 0, ring_size = 0;
     if (tc)
         tc_ring((int)precision, &ring_off, &ring_size);
+    else if (cplx)
+        cplx_ring(&ring_off, &ring_size);
     else
         fma_ring(esz, &ring_off, &ring_size);
+    // complex plans: the scalar table, 4 components per instance in the
+    // component type (16 or 32 bytes), uploaded before the programs that
+    // point into it are built
+    size_t scal_bytes = 0;
+    const uint32_t scal_stride = (uint32_t)(2 * esz);
+    if (cplx) {
+        scal_bytes = std::max<size_t>(16, (size_t)count * scal_stride);
+        std::vector<char> host(scal_bytes, 0);
+        for (int64_t i = 0; i < count; ++i)
+            for (int c = 0; c < 4; ++c) {
+                if (dt == IAAT_C32) {
+                    const float v = (float)cscal[4 * i + c];
+                    std::memcpy(host.data() + i * scal_stride + c * 4, &v, 4);
+                } else {
+                    std::memcpy(host.data() + i * scal_stride + c * 8, &cscal[4 * i + c], 8);
+                }
+            }
+        if ((e = cudaMalloc(&plan->d_scal, scal_bytes)) != cudaSuccess) {
+            iaat_plan_destroy(plan);
+            return fail(IAAT_ERR_OOM, "cudaMalloc of the scalar table: %s", cudaGetErrorString(e));
+        }
+        if ((e = cudaMemcpy(plan->d_scal, host.data(), scal_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            iaat_plan_destroy(plan);
+            return cuda_fail(e, "upload the scalar table");
+        }
+    }
     std::vector<char> prog;
     std::vector<int64_t> poff;
-    iaat_status_t bs = build_programs(flat, gbeg, packs, pbeg, esz, tc, plan->grid, ring_off, ring_size, prog, poff);
+    iaat_status_t bs = build_programs(flat, gbeg, packs, pbeg, esz, tc, plan->grid, ring_off, ring_size,
+                                      cplx ? plan->d_scal : nullptr, scal_stride, prog, poff);
     if (bs != IAAT_OK) {
-        delete plan;
+        iaat_plan_destroy(plan);
         return bs;
     }
     if (opts && opts->inject_fault == 1 && !prog.empty()) {
@@ -748,12 +814,58 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     info.tasks = plan->ntasks;
     info.groups = plan->ngroups;
     info.blocks = nblocks;
-    info.plan_bytes = (int64_t)(pb + ob + sizeof(int32_t));
+    info.plan_bytes = (int64_t)(pb + ob + sizeof(int32_t) + scal_bytes);
     info.grid = plan->grid;
     info.kernels = plan->ngroups > 0 ? 1 : 0;
     plan->info = info;
     *out = plan;
     return IAAT_OK;
+}
+
+extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t count, iaat_dtype_t dtype,
+                                          iaat_precision_t precision, const iaat_plan_options_t *opts,
+                                          iaat_plan_t *out)
+{
+    if (!out)
+        return fail(IAAT_ERR_INVALID_VALUE, "out is NULL");
+    *out = nullptr;
+    if (count < 0 || (count > 0 && !descs))
+        return fail(IAAT_ERR_INVALID_VALUE, "bad descriptor array");
+    if (dtype != IAAT_F32 && dtype != IAAT_F64)
+        return fail(IAAT_ERR_INVALID_VALUE, "unknown dtype %d (complex batches: iaat_plan_create_complex)",
+                    (int)dtype);
+    if (precision < IAAT_PREC_DEFAULT || precision > IAAT_PREC_6XBF16)
+        return fail(IAAT_ERR_INVALID_VALUE, "unknown precision %d", (int)precision);
+    if (precision != IAAT_PREC_DEFAULT && dtype == IAAT_F64)
+        return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");
+    return plan_create_impl(descs, count, dtype, precision, opts, nullptr, out);
+}
+
+extern "C" iaat_status_t iaat_plan_create_complex(const iaat_cgemm_desc_t *descs, int64_t count, iaat_dtype_t dtype,
+                                                  const iaat_plan_options_t *opts, iaat_plan_t *out)
+{
+    if (!out)
+        return fail(IAAT_ERR_INVALID_VALUE, "out is NULL");
+    *out = nullptr;
+    if (count < 0 || (count > 0 && !descs))
+        return fail(IAAT_ERR_INVALID_VALUE, "bad descriptor array");
+    if (dtype != IAAT_C32 && dtype != IAAT_C64)
+        return fail(IAAT_ERR_INVALID_VALUE, "iaat_plan_create_complex takes IAAT_C32 or IAAT_C64 (dtype %d)",
+                    (int)dtype);
+    std::vector<iaat_gemm_desc_t> proxy((size_t)count);
+    std::vector<double> scal((size_t)count * 4);
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_cgemm_desc_t &c = descs[i];
+        double v[4] = {c.alpha_re, c.alpha_im, c.beta_re, c.beta_im};
+        if (dtype == IAAT_C32)
+            for (double &x : v)
+                x = (double)(float)x;
+        std::memcpy(&scal[4 * i], v, sizeof v);
+        const double alpha = (v[0] != 0.0 || v[1] != 0.0) ? 1.0 : 0.0;
+        const double beta = (v[2] == 0.0 && v[3] == 0.0) ? 0.0 : (v[2] == 1.0 && v[3] == 0.0) ? 1.0 : 2.0;
+        proxy[i] = iaat_gemm_desc_t{c.M, c.N, c.K, c.lda, c.ldb, c.ldc, c.transA, c.transB, alpha, beta, c.A, c.B, c.C};
+    }
+    return plan_create_impl(proxy.data(), count, dtype, IAAT_PREC_DEFAULT, opts, scal.data(), out);
 }
 
 extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
@@ -768,9 +880,10 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
     kp.p.poff = plan->d_poff;
     kp.p.ngroups = (int32_t)plan->ngroups;
     kp.p.err = plan->d_err;
-    cudaError_t e = plan->precision != IAAT_PREC_DEFAULT
-                        ? launch_tc((int)plan->precision, kp, plan->grid, static_cast<cudaStream_t>(stream))
-                        : launch_fma(plan->esz == 4 ? 0 : 1, kp, plan->grid, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = is_complex(plan->dtype)              ? launch_cplx(plan->dtype, kp, plan->grid, s)
+                    : plan->precision != IAAT_PREC_DEFAULT ? launch_tc((int)plan->precision, kp, plan->grid, s)
+                                                           : launch_fma(plan->esz == 4 ? 0 : 1, kp, plan->grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "kernel launch");
     return IAAT_OK;
@@ -837,6 +950,8 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
         cudaFree(plan->d_poff);
     if (plan->d_err)
         cudaFree(plan->d_err);
+    if (plan->d_scal)
+        cudaFree(plan->d_scal);
     if (cur >= 0 && cur != plan->device)
         cudaSetDevice(cur);
     delete plan;
@@ -866,7 +981,7 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
         while (piece < kPieceRows && (int64_t)((M + piece - 1) / piece) * ((N + piece - 1) / piece) > kInline)
             piece *= 2;
     }
-    st = make_tasks(0, g, esz, false, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks,
+    st = make_tasks(0, g, esz == 4 ? IAAT_F32 : IAAT_F64, false, -1, (uint32_t)(esz == 4 ? max_group_bytes<4>() : max_group_bytes<8>()), tasks,
                     &nb, piece);
     if (st != IAAT_OK)
         return st;
@@ -878,7 +993,7 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaGetDevice");
-    st = prepare_device(dev, kernel_kind(esz, IAAT_PREC_DEFAULT));
+    st = prepare_device(dev, kernel_kind(esz == 4 ? IAAT_F32 : IAAT_F64, IAAT_PREC_DEFAULT));
     if (st != IAAT_OK)
         return st;
     KParams kp;
@@ -962,7 +1077,7 @@ iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, i
                 int c0, w;
                 piece_range(N, pn, pj, c0, w);
                 TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
-                const TileChoice t = choose_tiling(esz, h, w, Keff, -1);
+                const TileChoice t = choose_tiling(esz == 4 ? IAAT_F32 : IAAT_F64, h, w, Keff, -1);
                 d.variant = (uint8_t)t.variant;
                 d.nbm = (uint8_t)t.nbm;
                 d.nbn = (uint8_t)t.nbn;

@@ -13,9 +13,13 @@ cudaError_t measure_fma_peak(int dtype, double *gflops);   // 0 FP32 FFMA, 1 FP6
 cudaError_t prepare_tc(int precision);
 cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t stream);
 int tc_group_cap(int precision);        // largest stage footprint (bytes)
+// complex kernel (CGEMM / ZGEMM), dtype IAAT_C32 or IAAT_C64
+cudaError_t prepare_cplx(int dtype);
+cudaError_t launch_cplx(int dtype, const KParams &kp, int grid, cudaStream_t stream);
 // The staging ring of each kernel: byte offset from the shared-memory base and size.
 void fma_ring(int esz, uint32_t *off, uint32_t *bytes);
 void tc_ring(int precision, uint32_t *off, uint32_t *bytes);
+void cplx_ring(uint32_t *off, uint32_t *bytes);
 constexpr int kTcPackRows = 128;        // rows of one MMA tile
 constexpr int kTcPackCols = 128;        // columns of one MMA tile
 // Allocation-free planning into caller-supplied arrays (host.cpp); used by

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libiaat.so")
 
 IAAT_OP_N, IAAT_OP_T = 0, 1
-IAAT_F32, IAAT_F64 = 0, 1
+IAAT_F32, IAAT_F64, IAAT_C32, IAAT_C64 = 0, 1, 2, 3
 IAAT_PREC_DEFAULT, IAAT_PREC_3XBF16, IAAT_PREC_TF32, IAAT_PREC_FP16, IAAT_PREC_6XBF16 = 0, 1, 2, 3, 4
 STATUS = {0: "IAAT_OK", 1: "IAAT_ERR_INVALID_VALUE", 2: "IAAT_ERR_NOT_SMALL", 3: "IAAT_ERR_MISALIGNED",
           4: "IAAT_ERR_UNSUPPORTED", 5: "IAAT_ERR_CUDA", 6: "IAAT_ERR_DEVICE_TIMEOUT", 7: "IAAT_ERR_OOM"}
@@ -27,6 +27,13 @@ DESC_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("lda", "<i4"),
                        ("ldc", "<i4"), ("transA", "<i4"), ("transB", "<i4"), ("alpha", "<f8"),
                        ("beta", "<f8"), ("A", "<u8"), ("B", "<u8"), ("C", "<u8")])
 assert DESC_DTYPE.itemsize == 72
+
+#: numpy mirror of iaat_cgemm_desc_t (88 bytes)
+CDESC_DTYPE = np.dtype([("M", "<i4"), ("N", "<i4"), ("K", "<i4"), ("lda", "<i4"), ("ldb", "<i4"),
+                        ("ldc", "<i4"), ("transA", "<i4"), ("transB", "<i4"), ("alpha_re", "<f8"),
+                        ("alpha_im", "<f8"), ("beta_re", "<f8"), ("beta_im", "<f8"), ("A", "<u8"),
+                        ("B", "<u8"), ("C", "<u8")])
+assert CDESC_DTYPE.itemsize == 88
 
 
 class IaatError(RuntimeError):
@@ -68,6 +75,9 @@ def lib():
         L.iaat_plan_create.restype = S
         L.iaat_plan_create.argtypes = [P, ctypes.c_int64, I, I, ctypes.POINTER(PlanOptions),
                                        ctypes.POINTER(ctypes.c_void_p)]
+        L.iaat_plan_create_complex.restype = S
+        L.iaat_plan_create_complex.argtypes = [P, ctypes.c_int64, I, ctypes.POINTER(PlanOptions),
+                                               ctypes.POINTER(ctypes.c_void_p)]
         L.iaat_gemm_grouped_noalloc.restype = S
         L.iaat_gemm_grouped_noalloc.argtypes = [P, ctypes.c_int64, I, P]
         L.iaat_gemm_grouped.restype = S
@@ -153,6 +163,17 @@ def iaat_plan_create(descs, dtype, precision=IAAT_PREC_DEFAULT, *, max_group_tas
     return Plan(h.value)
 
 
+def iaat_plan_create_complex(descs, dtype, *, max_group_tasks=0, force_variant=0, inject_fault=0):
+    """descs: numpy array of CDESC_DTYPE (device pointers inside); dtype
+    IAAT_C32 or IAAT_C64."""
+    descs = np.ascontiguousarray(descs, dtype=CDESC_DTYPE)
+    opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault)
+    h = ctypes.c_void_p()
+    _check(lib().iaat_plan_create_complex(descs.ctypes.data if len(descs) else None, len(descs), dtype,
+                                          ctypes.byref(opts), ctypes.byref(h)))
+    return Plan(h.value)
+
+
 def iaat_gemm_grouped_noalloc(descs, dtype, stream=None):
     """Allocation-free grouped GEMM (see include/iaat.h): descs is a
     DESC_DTYPE array with device pointers inside."""
@@ -221,6 +242,25 @@ def descs_for_pools(batch, baseA, baseB, baseC):
     d["transB"] = batch.transB
     d["alpha"] = batch.alpha
     d["beta"] = batch.beta
+    esz = batch.esize
+    d["A"] = np.uint64(baseA) + batch.offA.astype(np.uint64) * np.uint64(esz)
+    d["B"] = np.uint64(baseB) + batch.offB.astype(np.uint64) * np.uint64(esz)
+    d["C"] = np.uint64(baseC) + batch.offC.astype(np.uint64) * np.uint64(esz)
+    return d
+
+
+def cdescs_for_pools(batch, baseA, baseB, baseC):
+    """iaat_cgemm_desc_t array for a complex workloads.Batch whose pools sit
+    at device addresses baseA/baseB/baseC."""
+    d = np.zeros(batch.count, dtype=CDESC_DTYPE)
+    for f in ("M", "N", "K", "lda", "ldb", "ldc"):
+        d[f] = getattr(batch, f)
+    d["transA"] = batch.transA
+    d["transB"] = batch.transB
+    al = np.asarray(batch.alpha, np.complex128)
+    be = np.asarray(batch.beta, np.complex128)
+    d["alpha_re"], d["alpha_im"] = al.real, al.imag
+    d["beta_re"], d["beta_im"] = be.real, be.imag
     esz = batch.esize
     d["A"] = np.uint64(baseA) + batch.offA.astype(np.uint64) * np.uint64(esz)
     d["B"] = np.uint64(baseB) + batch.offB.astype(np.uint64) * np.uint64(esz)

@@ -28,14 +28,27 @@ def gather_index(batch, which, idx=None):
     return off[inst] + (loc // rr) * ld[inst] + loc % rr, cnt
 
 
+DTYPES = {np.float32: iaat.IAAT_F32, np.float64: iaat.IAAT_F64,
+          np.complex64: iaat.IAAT_C32, np.complex128: iaat.IAAT_C64}
+
+
 def to_device(batch):
     import torch
     dev = torch.device("cuda:0")
     tA = torch.from_numpy(batch.A).to(dev)
     tB = torch.from_numpy(batch.B).to(dev)
     tC = torch.from_numpy(batch.C).to(dev)
-    descs = iaat.descs_for_pools(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+    make = iaat.cdescs_for_pools if batch.is_complex else iaat.descs_for_pools
+    descs = make(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
     return tA, tB, tC, descs
+
+
+def plan_for(batch, descs, precision=iaat.IAAT_PREC_DEFAULT, **plan_kw):
+    """iaat_plan_create, or iaat_plan_create_complex for a complex batch."""
+    dtype = DTYPES[np.dtype(batch.dtype).type]
+    if batch.is_complex:
+        return iaat.iaat_plan_create_complex(descs, dtype, **plan_kw)
+    return iaat.iaat_plan_create(descs, dtype, precision, **plan_kw)
 
 
 def run_grouped(batch, precision=iaat.IAAT_PREC_DEFAULT, **plan_kw):
@@ -43,8 +56,7 @@ def run_grouped(batch, precision=iaat.IAAT_PREC_DEFAULT, **plan_kw):
     plan info."""
     import torch
     tA, tB, tC, descs = to_device(batch)
-    dtype = iaat.IAAT_F32 if batch.dtype == np.float32 else iaat.IAAT_F64
-    plan = iaat.iaat_plan_create(descs, dtype, precision, **plan_kw)
+    plan = plan_for(batch, descs, precision, **plan_kw)
     s = torch.cuda.current_stream()
     iaat.iaat_gemm_grouped(plan, s)
     iaat.iaat_plan_check(plan, s)
@@ -58,7 +70,8 @@ def compare(batch, Cpool, idx=None, nthreads=0):
     """Errors of the GPU result against the oracle on instances idx."""
     if idx is None:
         idx = np.arange(batch.count)
-    ref, _ = oracle.gemm_batch(batch, idx, nthreads=nthreads)
+    run = oracle.cgemm_batch if batch.is_complex else oracle.gemm_batch
+    ref, _ = run(batch, idx, nthreads=nthreads)
     return errors(batch, Cpool, ref, idx)
 
 
@@ -69,11 +82,13 @@ def errors(batch, Cpool, ref, idx=None):
     Returns dict: eps_batch = ||dC||_F / ||C_ref||_F over the selection, and
     the per-instance guarded error
     eps_i = ||dC_i||_F / (|alpha| ||opA_i||_F ||opB_i||_F + |beta| ||C0_i||_F)
-    (max, median, rms), plus 'exact' (all elements equal)."""
+    (max, median, rms), plus 'exact' (all elements equal).  Complex batches
+    take complex differences and moduli."""
     if idx is None:
         idx = np.arange(batch.count)
+    cast = np.complex128 if np.iscomplexobj(Cpool) else np.float64
     gi, cnt = gather_index(batch, "C", idx)
-    got = Cpool[gi].astype(np.float64)
+    got = Cpool[gi].astype(cast)
     d = got - ref
     nref = np.linalg.norm(ref)
     ndiff = np.linalg.norm(d)
@@ -90,15 +105,15 @@ def errors(batch, Cpool, ref, idx=None):
         if len(counts) > 1:
             st[1:] = np.cumsum(counts)[:-1]
         if nz.any():
-            s[nz] = np.add.reduceat(v * v, st[nz])[: nz.sum()] if len(v) else 0
+            s[nz] = np.add.reduceat(np.abs(v) ** 2, st[nz])[: nz.sum()] if len(v) else 0
         return np.sqrt(s)
 
     dn = seg_norm(d, cnt)
     ia, ca = gather_index(batch, "A", idx)
     ib, cb = gather_index(batch, "B", idx)
-    nA = seg_norm(batch.A[ia].astype(np.float64), ca)
-    nB = seg_norm(batch.B[ib].astype(np.float64), cb)
-    nC = seg_norm(batch.C[gi].astype(np.float64), cnt)
+    nA = seg_norm(batch.A[ia].astype(cast), ca)
+    nB = seg_norm(batch.B[ib].astype(cast), cb)
+    nC = seg_norm(batch.C[gi].astype(cast), cnt)
     al = np.abs(batch.alpha[idx])
     be = np.abs(batch.beta[idx])
     den = al * nA * nB + be * nC
@@ -121,6 +136,6 @@ def padding_untouched(batch, Cpool):
     gi, _ = gather_index(batch, "C")
     mask = np.ones(len(Cpool), bool)
     mask[gi] = False
-    a = Cpool[mask].view(np.uint32 if Cpool.dtype == np.float32 else np.uint64)
-    b = batch.C[mask].view(a.dtype)
+    a = Cpool[mask].view(np.uint8)
+    b = batch.C[mask].view(np.uint8)
     return bool(np.array_equal(a, b))

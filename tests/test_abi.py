@@ -111,3 +111,65 @@ def test_quick_returns_touch_nothing(L):
     iaat.iaat_sgemm(0, 0, 0, 5, 5, 1.0, 0, 1, 0, 5, 0.0, 0, 1)
     iaat.iaat_sgemm(0, 0, 5, 0, 5, 1.0, 0, 5, 0, 5, 0.0, 0, 5)
     iaat.iaat_sgemm(0, 0, 5, 5, 5, 0.0, 0, 5, 0, 5, 1.0, 0x3000, 5)
+
+
+def _cdesc(**kw):
+    d = np.zeros(1, iaat.CDESC_DTYPE)
+    base = dict(M=4, N=4, K=4, lda=4, ldb=4, ldc=4, transA=0, transB=0, alpha_re=1.0, alpha_im=0.5,
+                beta_re=0.0, beta_im=0.0, A=0x10000, B=0x20000, C=0x30000)
+    base.update(kw)
+    for k, v in base.items():
+        d[k] = v
+    return d
+
+
+@pytest.mark.parametrize("dtype", [iaat.IAAT_C32, iaat.IAAT_C64])
+@pytest.mark.parametrize("kw,status", [
+    (dict(M=-1), 1), (dict(lda=3), 1), (dict(ldc=3), 1), (dict(transB=2), 1), (dict(C=0), 1),
+    (dict(M=80, N=80, K=81, lda=80, ldb=81, ldc=80), 2),
+    (dict(M=32, N=32, K=33, transA=1, lda=33, ldb=33, ldc=32), 2),
+    (dict(A=0x10004), 3),
+])
+def test_complex_plan_create_rejects(L, dtype, kw, status):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create_complex(_cdesc(**kw), dtype)
+    assert e.value.status == status
+    assert "instance 0" in e.value.message
+
+
+def test_complex_alignment_is_the_element_size(L):
+    """A pointer 8 bytes past a 16-byte boundary is aligned for complex float
+    but not for complex double (elements of 8 and 16 bytes)."""
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create_complex(_cdesc(C=0x30008), iaat.IAAT_C64)
+    assert e.value.status == 3
+    with pytest.raises(iaat.IaatError) as e:   # passes the alignment check, fails the next one
+        iaat.iaat_plan_create_complex(_cdesc(C=0x30008, ldc=3), iaat.IAAT_C32)
+    assert e.value.status == 1
+
+
+def test_complex_dtypes_have_their_own_entry(L):
+    """iaat_plan_create refuses complex dtypes; iaat_plan_create_complex
+    refuses real ones."""
+    for dt in (iaat.IAAT_C32, iaat.IAAT_C64, 4):
+        with pytest.raises(iaat.IaatError) as e:
+            iaat.iaat_plan_create(_desc(), dt)
+        assert e.value.status == 1
+    for dt in (iaat.IAAT_F32, iaat.IAAT_F64, -1, 4):
+        with pytest.raises(iaat.IaatError) as e:
+            iaat.iaat_plan_create_complex(_cdesc(), dt)
+        assert e.value.status == 1
+
+
+def test_complex_tiler_uses_the_complex_family():
+    """The host tiler covers C exactly for every dtype; complex double tiles
+    are at most 32 x 16 or 16 x 32 (its register-tile family)."""
+    for dt in (iaat.IAAT_C32, iaat.IAAT_C64):
+        for M, N, K in [(1, 1, 1), (15, 15, 15), (33, 17, 9), (80, 80, 80), (64, 5, 80)]:
+            blocks = iaat.iaat_tile(dt, 0, 0, M, N, K)
+            cover = np.zeros((M, N), int)
+            for r0, c0, h, w in blocks:
+                cover[r0:r0 + h, c0:c0 + w] += 1
+                if dt == iaat.IAAT_C64:
+                    assert h * w <= 512, (M, N, K, h, w)
+            assert (cover == 1).all(), (dt, M, N, K)
