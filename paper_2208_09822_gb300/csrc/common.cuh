@@ -206,21 +206,32 @@ constexpr Variant kVariantsF64[kNumVariantsF64] = {
 // Complex families (CGEMM / ZGEMM, Table I rows 3-4): an accumulator is a
 // (re, im) pair, so a complex-float tile takes the registers of an FP64 tile
 // of the same shape and a complex-double tile twice that; the complex-double
-// tiles are half the size.
-constexpr int kNumVariantsC = 5;
-constexpr Variant kVariantsC32[kNumVariantsC] = {
+// tiles are at most 32 x 16.  Complex double runs at the DFMA rate, where
+// every lane of a partly filled block costs a DFMA slot, so its family adds
+// one-element-per-lane tiles in every lane-grid shape: with them the tiler
+// fills about 80% of the DFMA slots on log-uniform sizes in [1, 80],
+// against about 61% with the five larger tiles alone (flop-weighted model).
+constexpr int kNumVariantsC32 = 5;
+constexpr Variant kVariantsC32[kNumVariantsC32] = {
     {4, 8, 8, 4},   // 0: 32 x 32
     {4, 4, 8, 4},   // 1: 32 x 16
     {4, 4, 4, 8},   // 2: 16 x 32
     {2, 4, 8, 4},   // 3: 16 x 16
     {1, 2, 8, 4},   // 4: 8 x 8
 };
-constexpr Variant kVariantsC64[kNumVariantsC] = {
-    {4, 4, 8, 4},   // 0: 32 x 16
-    {4, 4, 4, 8},   // 1: 16 x 32
-    {2, 4, 8, 4},   // 2: 16 x 16
-    {2, 2, 8, 4},   // 3: 16 x 8
-    {1, 2, 8, 4},   // 4: 8 x 8
+constexpr int kNumVariantsC64 = 11;
+constexpr Variant kVariantsC64[kNumVariantsC64] = {
+    {4, 4, 8, 4},    // 0: 32 x 16
+    {4, 4, 4, 8},    // 1: 16 x 32
+    {2, 4, 8, 4},    // 2: 16 x 16
+    {2, 2, 8, 4},    // 3: 16 x 8
+    {1, 2, 8, 4},    // 4: 8 x 8
+    {1, 1, 8, 4},    // 5: 8 x 4
+    {1, 1, 4, 8},    // 6: 4 x 8
+    {1, 1, 16, 2},   // 7: 16 x 2
+    {1, 1, 2, 16},   // 8: 2 x 16
+    {1, 1, 32, 1},   // 9: 32 x 1
+    {1, 1, 1, 32},   // 10: 1 x 32
 };
 
 // K is consumed in chunks of kKC (FP32) / kKC64 (FP64) staged per warp.

@@ -87,10 +87,10 @@ static const Variant *variants(int dt, int *n)
         *n = kNumVariantsF32;
         return kVariantsF32;
     case IAAT_C32:
-        *n = kNumVariantsC;
+        *n = kNumVariantsC32;
         return kVariantsC32;
     case IAAT_C64:
-        *n = kNumVariantsC;
+        *n = kNumVariantsC64;
         return kVariantsC64;
     default:
         *n = kNumVariantsF64;
@@ -106,12 +106,17 @@ double model_block_cost(const Variant &v, int esz, int K);
 
 // Complex tiles read the staged operands in place: per k term MR + NR
 // element loads and 4*MR*NR FMAs (Eq. 2's four real products per complex
-// one; DFMA-weighted for complex double), then a complex epilogue.
+// one), then a complex epilogue.  Complex double is bound by the DFMA pipe,
+// which takes a warp's DFMA in 64 clocks while other instructions issue in
+// one and overlap it, so there a block costs almost only its DFMA slots --
+// idle lanes of a partly filled tile included.
+constexpr double kComplexDfmaWeight = 32.0;
+
 static double block_cost(const Variant &v, int dt, int K)
 {
     if (!is_complex(dt))
         return iaat::model_block_cost(v, dtype_esz(dt), K);
-    const double fma = 4.0 * v.mr * v.nr * (dt == IAAT_C64 ? tuning().dfma_weight : 1.0);
+    const double fma = 4.0 * v.mr * v.nr * (dt == IAAT_C64 ? kComplexDfmaWeight : 1.0);
     return (double)K * (fma + v.mr + v.nr) + 2.0 * tuning().epilogue_weight * v.mr * v.nr + tuning().block_overhead;
 }
 

@@ -163,7 +163,8 @@ def test_complex_dtypes_have_their_own_entry(L):
 
 def test_complex_tiler_uses_the_complex_family():
     """The host tiler covers C exactly for every dtype; complex double tiles
-    are at most 32 x 16 or 16 x 32 (its register-tile family)."""
+    are at most 32 x 16 or 16 x 32 (its register-tile family), and a
+    one-column C takes one-column tiles (no idle lane columns)."""
     for dt in (iaat.IAAT_C32, iaat.IAAT_C64):
         for M, N, K in [(1, 1, 1), (15, 15, 15), (33, 17, 9), (80, 80, 80), (64, 5, 80)]:
             blocks = iaat.iaat_tile(dt, 0, 0, M, N, K)
@@ -173,3 +174,7 @@ def test_complex_tiler_uses_the_complex_family():
                 if dt == iaat.IAAT_C64:
                     assert h * w <= 512, (M, N, K, h, w)
             assert (cover == 1).all(), (dt, M, N, K)
+    assert all(w == 1 for _, _, _, w in iaat.iaat_tile(iaat.IAAT_C64, 0, 0, 32, 1, 40))
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create_complex(_cdesc(), iaat.IAAT_C32, force_variant=6)
+    assert e.value.status == 1
