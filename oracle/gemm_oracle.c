@@ -143,7 +143,7 @@ int oracle_max_threads(void)
 }
 
 /*
- * Complex GEMM (CGEMM / ZGEMM; Table I rows 3-4 and the type list of Sec. I,
+ * Complex GEMM (CGEMM / ZGEMM; Table I rows 3-4 and the type list of Sec. III-A,
  * which name single- and double-precision complex matrix multiplication with
  * the same four cases NN, NT, TN, TT and no conjugation):
  *
