@@ -34,7 +34,9 @@ METRIC = "small-GEMM GFLOP/s & roofline % (uneven batch), TC split vs plain FP32
 WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT/TN/TT uniform "
             "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
 NOMINAL_HBM_GBS = 8000.0
-PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
+PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4, "3xbf16-k8ffma": 1}
+# paths that route small-K instances to the FP32 CUDA-core kernel (route_k_below)
+ROUTE = {"3xbf16-k8ffma": 8}
 
 # Batches bench.py can time.  The default is the uneven FP32 batch (the
 # headline); the others run the CUDA-core path of their type only:
@@ -231,8 +233,9 @@ def main():
     ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
     ap.add_argument("--precision", default="3xbf16", choices=sorted(PRECISIONS),
                     help="the headline path (the tensor-core FP32 split by default)")
-    ap.add_argument("--compare", default="ffma", type=lambda v: [x for x in v.split(",") if x],
-                    help="comma-separated paths timed beside the headline (plain FP32 by default)")
+    ap.add_argument("--compare", default="ffma,3xbf16-k8ffma", type=lambda v: [x for x in v.split(",") if x],
+                    help="comma-separated paths timed beside the headline (plain FP32 and the 3xBF16 plan "
+                         "that routes K < 8 to FP32 by default)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="instance ranges the end-to-end leg pipelines copies and launches over")
@@ -279,8 +282,10 @@ def main():
     if not args.no_autotune and not os.environ.get("IAAT_TUNE_CACHE") and wl_dtype in (0, 1):
         t0 = time.time()
         if wl_dtype == 0:
-            for name in dict.fromkeys([args.precision] + list(args.compare)):
-                iaat.iaat_autotune(iaat.IAAT_F32, PRECISIONS[name], None)
+            names = [args.precision] + list(args.compare)
+            precs = [PRECISIONS[n] for n in names] + [0 for n in names if n in ROUTE]
+            for p in dict.fromkeys(precs):
+                iaat.iaat_autotune(iaat.IAAT_F32, p, None)
         else:
             iaat.iaat_autotune(iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT, None)
         tuned = f"autotuned at start-up ({time.time() - t0:.1f} s, outside the timed region)"
@@ -300,7 +305,7 @@ def main():
 
     def make_plan(d, name):
         if wl_dtype == 0:
-            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name])
+            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name], route_k_below=ROUTE.get(name, 0))
         if wl_dtype == 1:
             return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
         return iaat.iaat_plan_create_complex(d, wl_dtype)
@@ -479,7 +484,7 @@ def main():
         paths = {}
         for name, (inf, ms_p, _) in results.items():
             paths[name] = {"value": inf["flops"] * world / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
-                           "ms_per_step": ms_p,
+                           "ms_per_step": ms_p, "launches_per_step": inf["kernels"],
                            "roofline_frac": inf["algorithmic_bytes"] / (ms_p * 1e-3) / 1e9 / peaks["hbm_gbs"],
                            "error": errs.get(name)}
         if dfma_bound:

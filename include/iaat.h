@@ -125,7 +125,13 @@ typedef struct {
     int32_t inject_fault;      /* testing only: 1 = corrupt the first stage's task
                                   count so the kernel must detect it, give up and
                                   report IAAT_ERR_DEVICE_TIMEOUT via iaat_plan_check */
-    int32_t reserved[4];
+    int32_t route_k_below;     /* tensor-core plans only: instances with K below this
+                                  value run on the FP32 CUDA-core kernel instead, in
+                                  the same iaat_gemm_grouped call (a second launch on
+                                  the same stream).  The split's dropped low-low term
+                                  is not averaged out at tiny K; with 8, every
+                                  instance meets FP32-like accuracy.  0: no routing */
+    int32_t reserved[3];
 } iaat_plan_options_t;
 
 /* Statistics of a plan (iaat_plan_info). */
@@ -134,13 +140,15 @@ typedef struct {
     int64_t active;            /* instances that need work */
     int64_t tasks;             /* work pieces after splitting */
     int64_t groups;            /* pipeline stages */
-    int64_t blocks;            /* warp blocks over all tasks (tensor-core plans: MMA packs) */
+    int64_t blocks;            /* warp blocks over all tasks (tensor-core plans: MMA
+                                  packs, plus the warp blocks of routed instances) */
     int64_t flops;             /* sum of 2*M*N*K over active instances (Eq. 1);
                                   complex plans 8*M*N*K (Eq. 2) */
     int64_t algorithmic_bytes; /* A, B, C written, C read when beta != 0 */
     int64_t plan_bytes;        /* device bytes the plan holds (descriptors) */
     int32_t grid;              /* CTAs of each launch */
-    int32_t kernels;           /* kernels one iaat_gemm_grouped launches */
+    int32_t kernels;           /* kernels one iaat_gemm_grouped launches (2 when a
+                                  tensor-core plan routes small-K instances) */
     int32_t dtype, precision;
 } iaat_plan_info_t;
 

@@ -262,6 +262,7 @@ struct iaat_plan_s {
     int64_t *d_poff = nullptr;     // program offset per group
     int32_t *d_err = nullptr;
     char *d_scal = nullptr;        // complex plans: alpha, beta of every instance
+    iaat_plan_s *sub = nullptr;    // routed plans: the FP32 CUDA-core plan of the small-K instances
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
     iaat_plan_info_t info{};
@@ -670,10 +671,11 @@ iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vecto
 // The planner behind iaat_plan_create and iaat_plan_create_complex.  cscal:
 // complex plans only, (re alpha, im alpha, re beta, im beta) per instance,
 // already rounded to the component type; the descriptors then carry alpha
-// and beta as markers (see make_tasks).
+// and beta as markers (see make_tasks).  index_map: the caller's index of
+// each descriptor, for error messages (NULL: the position itself).
 static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t count, int dt,
                                       iaat_precision_t precision, const iaat_plan_options_t *opts,
-                                      const double *cscal, iaat_plan_t *out)
+                                      const double *cscal, iaat_plan_t *out, const int64_t *index_map = nullptr)
 {
     const int esz = dtype_esz(dt);
     const bool tc = precision != IAAT_PREC_DEFAULT;
@@ -713,12 +715,14 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     int64_t nblocks = 0;
     for (int64_t i = 0; i < count; ++i) {
         const iaat_gemm_desc_t &g = descs[i];
-        iaat_status_t st = check_instance(i, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+        const int64_t gi = index_map ? index_map[i] : i;
+        iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
                                           g.alpha, esz);
         if (st != IAAT_OK)
             return st;
         const size_t before = tasks.size();
-        st = make_tasks(i, g, dt, tc, force_variant, cap, tasks, &nblocks);
+        // complex plans index their scalar table by position (never remapped)
+        st = make_tasks(cplx ? i : gi, g, dt, tc, force_variant, cap, tasks, &nblocks);
         if (st != IAAT_OK)
             return st;
         if (tasks.size() > before) {
@@ -843,7 +847,59 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         return fail(IAAT_ERR_INVALID_VALUE, "unknown precision %d", (int)precision);
     if (precision != IAAT_PREC_DEFAULT && dtype == IAAT_F64)
         return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");
-    return plan_create_impl(descs, count, dtype, precision, opts, nullptr, out);
+    if (opts && opts->route_k_below < 0)
+        return fail(IAAT_ERR_INVALID_VALUE, "route_k_below %d is negative", opts->route_k_below);
+    if (precision == IAAT_PREC_DEFAULT || !opts || opts->route_k_below == 0)
+        return plan_create_impl(descs, count, dtype, precision, opts, nullptr, out);
+
+    // Routed tensor-core plan: instances with K below route_k_below (or
+    // alpha == 0, which reads neither A nor B) go to an FP32 CUDA-core plan
+    // that the same iaat_gemm_grouped call launches after the tensor-core
+    // one.  Every instance is validated first so errors name the caller's
+    // index; each part then keeps those indices through index_map.
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        const iaat_status_t st = check_instance(i, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B,
+                                                g.C, g.alpha, 4);
+        if (st != IAAT_OK)
+            return st;
+    }
+    std::vector<iaat_gemm_desc_t> dtc, dfma;
+    std::vector<int64_t> itc, ifma;
+    for (int64_t i = 0; i < count; ++i) {
+        const int keff = descs[i].alpha == 0.0 ? 0 : descs[i].K;
+        (keff < opts->route_k_below ? dfma : dtc).push_back(descs[i]);
+        (keff < opts->route_k_below ? ifma : itc).push_back(i);
+    }
+    iaat_plan_options_t o = *opts;
+    o.route_k_below = 0;
+    iaat_plan_t main_plan = nullptr, sub = nullptr;
+    iaat_status_t st = plan_create_impl(dtc.data(), (int64_t)dtc.size(), IAAT_F32, precision, &o, nullptr, &main_plan,
+                                        itc.data());
+    if (st != IAAT_OK)
+        return st;
+    o.inject_fault = 0;
+    st = plan_create_impl(dfma.data(), (int64_t)dfma.size(), IAAT_F32, IAAT_PREC_DEFAULT, &o, nullptr, &sub,
+                          ifma.data());
+    if (st != IAAT_OK) {
+        iaat_plan_destroy(main_plan);
+        return st;
+    }
+    main_plan->sub = sub;
+    iaat_plan_info_t &a = main_plan->info;
+    const iaat_plan_info_t &b = sub->info;
+    a.instances = count;
+    a.active += b.active;
+    a.tasks += b.tasks;
+    a.groups += b.groups;
+    a.blocks += b.blocks;
+    a.flops += b.flops;
+    a.algorithmic_bytes += b.algorithmic_bytes;
+    a.plan_bytes += b.plan_bytes;
+    a.grid = std::max(a.grid, b.grid);
+    a.kernels += b.kernels;
+    *out = main_plan;
+    return IAAT_OK;
 }
 
 extern "C" iaat_status_t iaat_plan_create_complex(const iaat_cgemm_desc_t *descs, int64_t count, iaat_dtype_t dtype,
@@ -878,7 +934,7 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
     if (!plan)
         return fail(IAAT_ERR_INVALID_VALUE, "plan is NULL");
     if (plan->ngroups == 0)
-        return IAAT_OK;
+        return plan->sub ? iaat_gemm_grouped(plan->sub, stream) : IAAT_OK;
     KParams kp;
     std::memset(&kp, 0, sizeof kp);
     kp.p.prog = plan->d_prog;
@@ -891,6 +947,8 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
                                                            : launch_fma(plan->esz == 4 ? 0 : 1, kp, plan->grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "kernel launch");
+    if (plan->sub)   // routed small-K instances, after the tensor-core launch on the same stream
+        return iaat_gemm_grouped(plan->sub, stream);
     return IAAT_OK;
 }
 
@@ -913,21 +971,26 @@ static iaat_status_t read_and_clear(int32_t *d_err, cudaStream_t s)
 
 extern "C" iaat_status_t iaat_plan_check(iaat_plan_t plan, void *stream)
 {
-    int32_t *w = nullptr;
     if (plan) {
-        w = plan->d_err;
-    } else {
-        cudaError_t e = single_call_err_ptr(&w);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress");
-        int32_t *w2 = nullptr;
-        if ((e = noalloc_err_ptr(&w2)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetDevice");
-        if (w2) {
-            const iaat_status_t st = read_and_clear(w2, static_cast<cudaStream_t>(stream));
-            if (st != IAAT_OK)
-                return st;
+        iaat_status_t st = read_and_clear(plan->d_err, static_cast<cudaStream_t>(stream));
+        if (plan->sub) {
+            const iaat_status_t s2 = iaat_plan_check(plan->sub, stream);
+            if (st == IAAT_OK)
+                st = s2;
         }
+        return st;
+    }
+    int32_t *w = nullptr;
+    cudaError_t e = single_call_err_ptr(&w);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress");
+    int32_t *w2 = nullptr;
+    if ((e = noalloc_err_ptr(&w2)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (w2) {
+        const iaat_status_t st = read_and_clear(w2, static_cast<cudaStream_t>(stream));
+        if (st != IAAT_OK)
+            return st;
     }
     return read_and_clear(w, static_cast<cudaStream_t>(stream));
 }
@@ -944,6 +1007,8 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
 {
     if (!plan)
         return IAAT_OK;
+    if (plan->sub)
+        iaat_plan_destroy(plan->sub);
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != plan->device)

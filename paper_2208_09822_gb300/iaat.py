@@ -46,7 +46,7 @@ class IaatError(RuntimeError):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("max_group_tasks", ctypes.c_int32),
                 ("force_variant", ctypes.c_int32), ("inject_fault", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("route_k_below", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -153,10 +153,10 @@ class Plan:
 
 
 def iaat_plan_create(descs, dtype, precision=IAAT_PREC_DEFAULT, *, max_group_tasks=0, force_variant=0,
-                     inject_fault=0):
+                     inject_fault=0, route_k_below=0):
     """descs: numpy array of DESC_DTYPE (device pointers inside)."""
     descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
-    opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault)
+    opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault, route_k_below)
     h = ctypes.c_void_p()
     _check(lib().iaat_plan_create(descs.ctypes.data if len(descs) else None, len(descs), dtype, precision,
                                   ctypes.byref(opts), ctypes.byref(h)))

@@ -178,3 +178,15 @@ def test_complex_tiler_uses_the_complex_family():
     with pytest.raises(iaat.IaatError) as e:
         iaat.iaat_plan_create_complex(_cdesc(), iaat.IAAT_C32, force_variant=6)
     assert e.value.status == 1
+
+
+def test_routed_plan_validates_with_caller_indices(L):
+    """A routed tensor-core plan checks every instance before splitting, so
+    the error names the caller's index; a negative threshold is refused."""
+    d = np.concatenate([_desc(K=2), _desc(K=20, ldb=20), _desc(K=3), _desc(K=30, ldb=30, ldc=3)])
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(d, iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=8)
+    assert e.value.status == 1 and "instance 3" in e.value.message
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=-1)
+    assert e.value.status == 1

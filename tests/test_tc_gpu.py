@@ -141,3 +141,61 @@ def test_3xbf16_graph_replay(cuda):
     err = compare(b, tC.cpu().numpy())
     assert err["eps_batch"] <= 1e-5, err
     plan.destroy()
+
+
+def test_3xbf16_routed_small_k(cuda):
+    """A 3xBF16 plan that routes K < 8 to the FP32 CUDA-core kernel: every
+    instance's guarded error is within 1e-5 (plain 3xBF16 misses it at K of
+    1-2), one call launches both kernels, and each part's result is bit for
+    bit what the unrouted plan of its own path gives (an instance's result
+    does not depend on which others share its plan)."""
+    torch = cuda
+    b = W.uneven(count=40000, seed=24)
+    tA, tB, tC, descs = to_device(b)
+    C0 = tC.clone()
+    s = torch.cuda.current_stream()
+    out = {}
+    for name, prec, route in (("routed", iaat.IAAT_PREC_3XBF16, 8), ("tc", iaat.IAAT_PREC_3XBF16, 0),
+                              ("fma", iaat.IAAT_PREC_DEFAULT, 0)):
+        tC.copy_(C0)
+        plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, prec, route_k_below=route)
+        iaat.iaat_gemm_grouped(plan, s)
+        iaat.iaat_plan_check(plan, s)
+        out[name] = (tC.cpu().numpy(), iaat.iaat_plan_info(plan))
+        plan.destroy()
+    C, info = out["routed"]
+    assert info["kernels"] == 2 and info["instances"] == b.count
+    assert info["flops"] == out["tc"][1]["flops"]
+    err = compare(b, C)
+    assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= 1e-5, err
+    assert padding_untouched(b, C)
+    from .gpu_util import gather_index
+    small = np.nonzero((b.K < 8) | (b.alpha == 0))[0]
+    large = np.setdiff1d(np.arange(b.count), small)
+    for idx, ref in ((small, out["fma"][0]), (large, out["tc"][0])):
+        gi, _ = gather_index(b, "C", idx)
+        assert np.array_equal(C[gi].view(np.uint32), ref[gi].view(np.uint32))
+
+
+def test_routed_plan_in_a_graph(cuda):
+    """Both launches of a routed plan are captured and replayed."""
+    torch = cuda
+    b = W.uneven(count=5000, seed=25)
+    tA, tB, tC, descs = to_device(b)
+    C0 = tC.clone()
+    plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        iaat.iaat_gemm_grouped(plan, s)
+    iaat.iaat_plan_check(plan, s)
+    first = tC.cpu().numpy()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        iaat.iaat_gemm_grouped(plan, s)
+    tC.copy_(C0)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        g.replay()
+    iaat.iaat_plan_check(plan, s)
+    assert np.array_equal(tC.cpu().numpy().view(np.uint32), first.view(np.uint32))
+    plan.destroy()
