@@ -8,6 +8,7 @@ CPU oracle as the reported baseline.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision ffma]
     python bench.py --workload uneven-c64 ...   # other batches (see WORKLOADS)
     python bench.py --impl reference ...   # the CPU oracle arm
+    python bench.py --pack-ablation        # pack-step share by size (Fig. 3 on this GPU)
 
 One step = one execution of the whole plan (one persistent kernel launch,
 replayed from a CUDA graph).  The pools (about 1.3 GB) are larger than the
@@ -225,6 +226,75 @@ def run_reference(args):
     return 0
 
 
+def run_pack_ablation(args):
+    """The GPU analogue of Fig. 3 (the share of a traditional GEMM's time spent
+    in its pack step).  For same-size FP32 batches (M = N = K = n, 4096
+    instances, tight ld, alpha = 1.25, beta = -0.75, each case) time: the
+    library's grouped GEMM on the operands where they are (no pack), the pack
+    step (op(A), op(B) copied into tight NN copies; one kernel), and the same
+    grouped GEMM on the packed copies.  share = pack / (pack + packed GEMM);
+    slowdown = (pack + packed GEMM) / no-pack.  CUDA events on the launch
+    stream, 3 untimed runs then `--steps` (at most 50) timed runs of each."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2208_09822_gb300 import build as B
+    B.build()
+    from paper_2208_09822_gb300 import iaat
+    from paper_2208_09822_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    reps = max(1, min(args.steps, 50))
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    launches = 0
+    for case in ("NN", "NT", "TN", "TT"):
+        for n in (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 80):
+            if not W.in_domain(n, n, n, *W.TRANS_CASES[case]):
+                continue
+            b = W.sweep(case, (n, n, n), count=4096)
+            tA = torch.from_numpy(b.A).to(dev)
+            tB = torch.from_numpy(b.B).to(dev)
+            tC = torch.from_numpy(b.C).to(dev)
+            descs = iaat.descs_for_pools(b, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+            direct = iaat.iaat_plan_create(descs, iaat.IAAT_F32)
+            pk = iaat.iaat_pack_create(descs, iaat.IAAT_F32)
+            packed = iaat.iaat_plan_create(pk.packed, iaat.IAAT_F32)
+            t_direct = timed(lambda: iaat.iaat_gemm_grouped(direct, stream))
+            t_pack = timed(lambda: iaat.iaat_pack_run(pk, stream))
+            t_packed = timed(lambda: iaat.iaat_gemm_grouped(packed, stream))
+            iaat.iaat_plan_check(direct, stream)
+            iaat.iaat_plan_check(packed, stream)
+            launches += 3 * (reps + 3)
+            rows.append({"case": case, "n": n, "no_pack_us": t_direct * 1e3, "pack_us": t_pack * 1e3,
+                         "gemm_on_packed_us": t_packed * 1e3, "pack_share": t_pack / (t_pack + t_packed),
+                         "slowdown_vs_no_pack": (t_pack + t_packed) / t_direct,
+                         "pack_GBs": pk.bytes_moved / (t_pack * 1e-3) / 1e9})
+            for x in (direct, packed, pk):
+                x.destroy()
+    print(json.dumps({"metric": "pack-step share of a packed small GEMM (GPU analogue of Fig. 3)",
+                      "unit": "fraction", "dtype": "f32", "data": "synthetic", "n_gpus": 1,
+                      "config": {"workload": "sweep: 4096 same-size FP32 instances per launch, M=N=K=n, "
+                                             "tight ld, alpha=1.25, beta=-0.75, U[-1,1], seed 1",
+                                 "reps": reps, "l2": "n <= 48 fits the 129 MB L2; no flush (an ablation)"},
+                      "rows": rows, "gpu_launches": launches}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,12 +315,16 @@ def main():
                          "timed on its CUDA-core path only (fc64, uneven-c32 = CGEMM, uneven-c64 = ZGEMM)")
     ap.add_argument("--instances", type=int, default=None,
                     help="instances of the batch (default: the workload's; smaller only for profiling captures)")
+    ap.add_argument("--pack-ablation", action="store_true",
+                    help="time the pack step against the no-pack path by size (prints its own JSON line)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the built-in cost model instead of tuning each path first")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.pack_ablation:
+        return run_pack_ablation(args)
 
     import torch
     import torch.distributed as dist

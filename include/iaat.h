@@ -243,6 +243,27 @@ iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t precision,
  * CUDA-core paths.  Synchronous; allocates a small scratch buffer. */
 iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops);
 
+/* The pack step of a conventional GEMM, for ablation only (the GPU analogue
+ * of Fig. 3, the share of the time a traditional GEMM spends packing; the
+ * library's own paths never pack).  iaat_pack_create validates the instances
+ * like iaat_plan_create (FP32 or FP64), allocates a device workspace and
+ * writes to the caller's host array `packed` (count entries) descriptors of
+ * the same GEMMs on packed operands: op(A) as a tight column-major M x K
+ * matrix and op(B) as a tight K x N one in the workspace, transA = transB = N,
+ * lda = max(1, M), ldb = max(1, K); C, ldc, alpha and beta unchanged
+ * (instances that read neither A nor B get NULL there).  *bytes_moved (may be
+ * NULL) receives the pack kernel's algorithmic bytes per run: op(A) and op(B)
+ * of every packed instance read once and written once.  iaat_pack_run
+ * enqueues the copy (one kernel) on `stream`; plan the packed descriptors with
+ * iaat_plan_create.  iaat_pack_destroy synchronises the device and frees the
+ * workspace, which the packed descriptors point into. */
+typedef struct iaat_pack_s *iaat_pack_t;
+iaat_status_t iaat_pack_create(const iaat_gemm_desc_t *descs, int64_t count,
+                               iaat_dtype_t dtype, iaat_gemm_desc_t *packed,
+                               int64_t *bytes_moved, iaat_pack_t *out);
+iaat_status_t iaat_pack_run(iaat_pack_t pack, void *stream);
+iaat_status_t iaat_pack_destroy(iaat_pack_t pack);
+
 /* Host-only view of the run-time tiler (no GPU needed).  Tiles one M x N
  * (x K) instance of the given type and case with the library's register-tile
  * variants (all four dtypes; complex ones with the complex family) and

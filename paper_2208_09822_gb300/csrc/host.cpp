@@ -1200,3 +1200,12 @@ iaat_status_t iaat::noalloc_prepare(int dev)
 }
 
 int iaat::noalloc_sm_count(int dev) { return sm_count(dev); }
+
+// Error reporting and validation for the other translation units (the pack
+// step of pack.cu).
+iaat_status_t iaat::host_fail(iaat_status_t st, const char *msg) { return fail(st, "%s", msg); }
+
+iaat_status_t iaat::validate_instance(int64_t idx, const iaat_gemm_desc_t &g, int esz)
+{
+    return check_instance(idx, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C, g.alpha, esz);
+}

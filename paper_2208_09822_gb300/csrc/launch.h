@@ -31,4 +31,8 @@ iaat_status_t noalloc_fail(iaat_status_t st, const char *msg);
 iaat_status_t noalloc_prepare(int dev);
 int noalloc_sm_count(int dev);
 cudaError_t noalloc_err_ptr(int32_t **p);   // NULL until the entry point's first call on the device
+// host.cpp: set the calling thread's error message and return st; the
+// argument checks of one instance (index idx in messages)
+iaat_status_t host_fail(iaat_status_t st, const char *msg);
+iaat_status_t validate_instance(int64_t idx, const iaat_gemm_desc_t &g, int esz);
 }  // namespace iaat

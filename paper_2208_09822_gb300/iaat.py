@@ -78,6 +78,13 @@ def lib():
         L.iaat_plan_create_complex.restype = S
         L.iaat_plan_create_complex.argtypes = [P, ctypes.c_int64, I, ctypes.POINTER(PlanOptions),
                                                ctypes.POINTER(ctypes.c_void_p)]
+        L.iaat_pack_create.restype = S
+        L.iaat_pack_create.argtypes = [P, ctypes.c_int64, I, P, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_void_p)]
+        L.iaat_pack_run.restype = S
+        L.iaat_pack_run.argtypes = [P, P]
+        L.iaat_pack_destroy.restype = S
+        L.iaat_pack_destroy.argtypes = [P]
         L.iaat_gemm_grouped_noalloc.restype = S
         L.iaat_gemm_grouped_noalloc.argtypes = [P, ctypes.c_int64, I, P]
         L.iaat_gemm_grouped.restype = S
@@ -172,6 +179,43 @@ def iaat_plan_create_complex(descs, dtype, *, max_group_tasks=0, force_variant=0
     _check(lib().iaat_plan_create_complex(descs.ctypes.data if len(descs) else None, len(descs), dtype,
                                           ctypes.byref(opts), ctypes.byref(h)))
     return Plan(h.value)
+
+
+class Pack:
+    """Owner of an iaat_pack_t (the ablation's pack step); destroyed with the
+    object.  ``packed`` holds the descriptors of the packed instances and
+    ``bytes_moved`` the pack kernel's algorithmic bytes per run."""
+
+    def __init__(self, handle, packed, bytes_moved):
+        self.handle = handle
+        self.packed = packed
+        self.bytes_moved = bytes_moved
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.handle:
+            lib().iaat_pack_destroy(self.handle)
+            self.handle = None
+
+
+def iaat_pack_create(descs, dtype):
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    packed = np.zeros(len(descs), DESC_DTYPE)
+    moved = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    _check(lib().iaat_pack_create(descs.ctypes.data if len(descs) else None, len(descs), dtype,
+                                  packed.ctypes.data if len(descs) else None, ctypes.byref(moved),
+                                  ctypes.byref(h)))
+    return Pack(h.value, packed, moved.value)
+
+
+def iaat_pack_run(pack, stream=None):
+    _check(lib().iaat_pack_run(pack.handle, _stream(stream)))
 
 
 def iaat_gemm_grouped_noalloc(descs, dtype, stream=None):

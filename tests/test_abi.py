@@ -190,3 +190,15 @@ def test_routed_plan_validates_with_caller_indices(L):
     with pytest.raises(iaat.IaatError) as e:
         iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=-1)
     assert e.value.status == 1
+
+
+def test_pack_create_validates_before_the_device(L):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_pack_create(_desc(), iaat.IAAT_C32)
+    assert e.value.status == 1
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_pack_create(np.concatenate([_desc(), _desc(ldc=3)]), iaat.IAAT_F32)
+    assert e.value.status == 1 and "instance 1" in e.value.message
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_pack_create(_desc(M=80, N=80, K=81, lda=80, ldb=81, ldc=80), iaat.IAAT_F64)
+    assert e.value.status == 2
