@@ -9,6 +9,7 @@ CPU oracle as the reported baseline.
     python bench.py --workload uneven-c64 ...   # other batches (see WORKLOADS)
     python bench.py --impl reference ...   # the CPU oracle arm
     python bench.py --pack-ablation        # pack-step share by size (Fig. 3 on this GPU)
+    python bench.py --sweep                # same-size batches M = N = K = n, every case and pipe
 
 One step = one execution of the whole plan (one persistent kernel launch,
 replayed from a CUDA graph).  The pools (about 1.3 GB) are larger than the
@@ -295,6 +296,78 @@ def run_pack_ablation(args):
     return 0
 
 
+def run_sweep(args):
+    """Same-size batches on the M = N = K diagonal of the sweep sizes (4096
+    instances per launch, tight ld, alpha = 1.25, beta = -0.75, U[-1,1],
+    seed 1), every case, on the FFMA, 3xBF16 and DFMA paths: device time per
+    launch (CUDA events, 3 untimed then `--steps` (at most 20) timed launches
+    back to back), GFLOP/s (Eq. 1) and the fraction of the roofline, the slower
+    of the algorithmic bytes at the measured copy bandwidth and the flops at
+    the path's pipe peak (measured FFMA / DFMA rates, the measured BF16 burst
+    rate for the useful 2*M*N*K of 3xBF16)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2208_09822_gb300 import build as B
+    B.build()
+    from paper_2208_09822_gb300 import iaat
+    from paper_2208_09822_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    reps = max(1, min(args.steps, 20))
+    peaks, peak_kind = measured_peaks()
+    pipe = {"ffma": iaat.iaat_fma_peak(iaat.IAAT_F32), "dfma": iaat.iaat_fma_peak(iaat.IAAT_F64),
+            "3xbf16": peaks["bf16_tflops"] * 1e3}
+    rows, launches = [], 0
+    for case in ("NN", "NT", "TN", "TT"):
+        for n in (1, 2, 4, 8, 16, 32, 48, 64, 80):
+            if not W.in_domain(n, n, n, *W.TRANS_CASES[case]):
+                continue
+            for dtype, paths in ((np.float32, ("ffma", "3xbf16")), (np.float64, ("dfma",))):
+                b = W.sweep(case, (n, n, n), dtype=dtype, count=4096)
+                tA = torch.from_numpy(b.A).to(dev)
+                tB = torch.from_numpy(b.B).to(dev)
+                tC = torch.from_numpy(b.C).to(dev)
+                descs = iaat.descs_for_pools(b, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+                for path in paths:
+                    plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32 if dtype == np.float32 else iaat.IAAT_F64,
+                                                 iaat.IAAT_PREC_3XBF16 if path == "3xbf16" else 0)
+                    info = iaat.iaat_plan_info(plan)
+                    with torch.cuda.stream(stream):
+                        for _ in range(3):
+                            iaat.iaat_gemm_grouped(plan, stream)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        e0.record(stream)
+                        for _ in range(reps):
+                            iaat.iaat_gemm_grouped(plan, stream)
+                        e1.record(stream)
+                    torch.cuda.synchronize()
+                    iaat.iaat_plan_check(plan, stream)
+                    ms = e0.elapsed_time(e1) / reps
+                    launches += reps + 3
+                    t_roof = max(info["algorithmic_bytes"] / (peaks["hbm_gbs"] * 1e9),
+                                 info["flops"] / (pipe[path] * 1e9))
+                    rows.append({"case": case, "n": n, "path": path, "us": ms * 1e3,
+                                 "gflops": info["flops"] / (ms * 1e-3) / 1e9,
+                                 "roofline_frac": t_roof / (ms * 1e-3),
+                                 "bound": "hbm" if info["algorithmic_bytes"] / (peaks["hbm_gbs"] * 1e9)
+                                 >= info["flops"] / (pipe[path] * 1e9) else path})
+                    plan.destroy()
+                del tA, tB, tC
+    print(json.dumps({"metric": "same-size sweep GFLOP/s and roofline fraction (M = N = K)", "unit": "GFLOP/s",
+                      "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": "sweep diagonal: 4096 same-size instances per launch, tight ld, "
+                                             "alpha=1.25, beta=-0.75, U[-1,1], seed 1", "reps": reps,
+                                 "peaks": {"hbm_gbs": peaks["hbm_gbs"], "kind": peak_kind,
+                                           "ffma_gflops": pipe["ffma"], "dfma_gflops": pipe["dfma"],
+                                           "bf16_gflops": pipe["3xbf16"]},
+                                 "l2": "n <= 48 fits the 129 MB L2; no flush"},
+                      "rows": rows, "gpu_launches": launches}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,6 +388,8 @@ def main():
                          "timed on its CUDA-core path only (fc64, uneven-c32 = CGEMM, uneven-c64 = ZGEMM)")
     ap.add_argument("--instances", type=int, default=None,
                     help="instances of the batch (default: the workload's; smaller only for profiling captures)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time same-size batches on the M = N = K diagonal (prints its own JSON line)")
     ap.add_argument("--pack-ablation", action="store_true",
                     help="time the pack step against the no-pack path by size (prints its own JSON line)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -325,6 +400,8 @@ def main():
         return run_reference(args)
     if args.pack_ablation:
         return run_pack_ablation(args)
+    if args.sweep:
+        return run_sweep(args)
 
     import torch
     import torch.distributed as dist

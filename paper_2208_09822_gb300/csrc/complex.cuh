@@ -183,6 +183,7 @@ __device__ void consumer_loop_c(const KParams &KP, const SmemMap &S, int warp)
 {
     const Params &P = KP.p;
     const int lane = (int)lane_id();
+    int rot = 0;   // blocks taken so far over the CTA's stages, modulo the warps
     for (int i = 0;; ++i) {
         const int g = sched_group(i, blockIdx.x, gridDim.x);
         if (g >= P.ngroups)
@@ -198,7 +199,9 @@ __device__ void consumer_loop_c(const KParams &KP, const SmemMap &S, int warp)
         const TaskRec *recs = S.recs(slot);
         const int nb = hd->nblocks;
         const int pre = hd->prefix[lane];
-        for (int b = warp; b < nb; b += kCplxWarps) {
+        // the rotation continues across stages, so the warp that takes a
+        // stage's extra block is a different one each time
+        for (int b = (warp - rot + kCplxWarps) % kCplxWarps; b < nb; b += kCplxWarps) {
             const int t = __popc(__ballot_sync(0xffffffffu, pre <= b));
             const int before = __shfl_sync(0xffffffffu, pre, t > 0 ? t - 1 : 0);
             const int lb = b - (t > 0 ? before : 0);
@@ -213,6 +216,7 @@ __device__ void consumer_loop_c(const KParams &KP, const SmemMap &S, int warp)
         __syncwarp();
         if (lane == 0)
             mbar_arrive(S.empty(slot));
+        rot = (rot + nb) % kCplxWarps;
     }
 }
 

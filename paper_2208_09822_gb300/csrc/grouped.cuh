@@ -756,6 +756,7 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
     const int lane = (int)lane_id();
     T *As = reinterpret_cast<T *>(S.base + kSmemCanon + warp * Traits<ESZ>::kCanonBytes);
     T *Bs = As + Traits<ESZ>::KC * kMaxBM;
+    int rot = 0;   // blocks taken so far over the CTA's stages, modulo the warps
     for (int i = 0;; ++i) {
         const int g = sched_group(i, blockIdx.x, gridDim.x);
         if (g >= P.ngroups)
@@ -770,7 +771,9 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
         const TaskRec *recs = S.recs(slot);
         const int nb = hd->nblocks;
         const int pre = hd->prefix[lane];
-        for (int b = warp; b < nb; b += Traits<ESZ>::kWarps) {
+        // the rotation continues across stages, so the warp that takes a
+        // stage's extra block is a different one each time
+        for (int b = (warp - rot + Traits<ESZ>::kWarps) % Traits<ESZ>::kWarps; b < nb; b += Traits<ESZ>::kWarps) {
             const int t = __popc(__ballot_sync(0xffffffffu, pre <= b));
             const int before = __shfl_sync(0xffffffffu, pre, t > 0 ? t - 1 : 0);
             const int lb = b - (t > 0 ? before : 0);
@@ -786,6 +789,7 @@ __device__ void consumer_loop(const KParams &KP, const SmemMap &S, int warp)
         __syncwarp();
         if (lane == 0)
             mbar_arrive(S.empty(slot));
+        rot = (rot + nb) % Traits<ESZ>::kWarps;
     }
 }
 

@@ -141,13 +141,17 @@ struct TileChoice {
 // scaled: weigh the variants by the autotuner's measured scales (the
 // CUDA-core kernel); the tensor-core planner only uses the cost as an
 // ordering key and takes the plain model, so that tuning the CUDA-core
-// kernel does not reorder tensor-core stages.
-static TileChoice choose_tiling(int dt, int M, int N, int K, int force_variant, bool scaled = true)
+// kernel does not reorder tensor-core stages.  min_blocks: the cheapest
+// tiling with at least that many warp blocks (else the one with the most).
+static TileChoice choose_tiling(int dt, int M, int N, int K, int force_variant, bool scaled = true,
+                                int min_blocks = 1)
 {
     int nv;
     const Variant *vs = variants(dt, &nv);
     scaled = scaled && !is_complex(dt);   // the autotuner calibrates the real families
     TileChoice best{0, 1, 1, 1e300};
+    bool best_ok = false;
+    int best_blocks = 0;
     for (int v = 0; v < nv; ++v) {
         if (force_variant >= 0 && v != force_variant)
             continue;
@@ -157,11 +161,20 @@ static TileChoice choose_tiling(int dt, int M, int N, int K, int force_variant, 
             continue;
         const double c =
             (double)nbm * nbn * block_cost(vs[v], dt, K) * (scaled ? tuning().variant_scale(dtype_esz(dt), v) : 1.0);
-        if (c < best.cost)
+        const bool ok = nbm * nbn >= min_blocks;
+        const bool better = ok ? (!best_ok || c < best.cost)
+                               : (!best_ok && (nbm * nbn > best_blocks || (nbm * nbn == best_blocks && c < best.cost)));
+        if (better) {
             best = TileChoice{v, nbm, nbn, c};
+            best_ok = ok;
+            best_blocks = nbm * nbn;
+        }
     }
     return best;
 }
+
+// Consumer warps of the CUDA-core kernels (real FP32, real FP64, complex).
+static int fma_warps(int dt) { return dt == IAAT_F32 ? Traits<4>::kWarps : (is_complex(dt) ? kCplxWarps : kConsumerWarps); }
 
 extern "C" int64_t iaat_tile(iaat_dtype_t dtype, int transA, int transB, int M, int N, int K, int32_t *blocks,
                              int64_t cap)
@@ -430,7 +443,19 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc
                 d.alpha = (double)idx;
                 d.beta = 0.0;
             }
-            const TileChoice t = choose_tiling(dt, h, w, Keff, force_variant, !tc);
+            // Parallelism of the consumer warps: the staging ring (two stage
+            // caps) holds about ring / bytes tasks of this size at a time, and
+            // only their blocks can be computed, so a task too large for the
+            // ring to hold one per warp is tiled into at least warps / that
+            // many blocks.
+            int min_blocks = 1;
+            if (!tc && piece == 0 && force_variant < 0) {
+                const uint32_t bytes = std::max<uint32_t>(1, plan_task(d, esz).total());
+                const int resident = (int)std::max<uint32_t>(1, 2 * cap / bytes);
+                if (resident < fma_warps(dt))
+                    min_blocks = (fma_warps(dt) + resident - 1) / resident;
+            }
+            const TileChoice t = choose_tiling(dt, h, w, Keff, force_variant, !tc, min_blocks);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
             d.nbn = (uint8_t)t.nbn;
