@@ -409,6 +409,17 @@ bool choose_split(const iaat_gemm_desc_t &g, int esz, int Keff, uint32_t cap, in
     }
 }
 
+// Parallelism of the consumer warps of a CUDA-core kernel: its staging ring
+// (two stage caps) holds about ring / bytes tasks of a task's size at a time,
+// and only their blocks can be computed, so a task too large for the ring to
+// hold one per warp is tiled into at least warps / that many blocks.
+static int stage_min_blocks(const TaskDesc &d, int dt, uint32_t cap)
+{
+    const uint32_t bytes = std::max<uint32_t>(1, plan_task(d, dtype_esz(dt)).total());
+    const int resident = (int)std::max<uint32_t>(1, 2 * cap / bytes);
+    return resident < fma_warps(dt) ? (fma_warps(dt) + resident - 1) / resident : 1;
+}
+
 // Build the tasks of one instance: one, or its pieces.  piece > 0: cut C into
 // pieces of at most piece x piece as well (the single-call path spreads one
 // instance over several SMs that way).
@@ -443,18 +454,7 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc
                 d.alpha = (double)idx;
                 d.beta = 0.0;
             }
-            // Parallelism of the consumer warps: the staging ring (two stage
-            // caps) holds about ring / bytes tasks of this size at a time, and
-            // only their blocks can be computed, so a task too large for the
-            // ring to hold one per warp is tiled into at least warps / that
-            // many blocks.
-            int min_blocks = 1;
-            if (!tc && piece == 0 && force_variant < 0) {
-                const uint32_t bytes = std::max<uint32_t>(1, plan_task(d, esz).total());
-                const int resident = (int)std::max<uint32_t>(1, 2 * cap / bytes);
-                if (resident < fma_warps(dt))
-                    min_blocks = (fma_warps(dt) + resident - 1) / resident;
-            }
+            const int min_blocks = (!tc && piece == 0 && force_variant < 0) ? stage_min_blocks(d, dt, cap) : 1;
             const TileChoice t = choose_tiling(dt, h, w, Keff, force_variant, !tc, min_blocks);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
@@ -1172,7 +1172,8 @@ iaat_status_t iaat::noalloc_plan(const iaat_gemm_desc_t *descs, int64_t count, i
                 int c0, w;
                 piece_range(N, pn, pj, c0, w);
                 TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
-                const TileChoice t = choose_tiling(esz == 4 ? IAAT_F32 : IAAT_F64, h, w, Keff, -1);
+                const int dt = esz == 4 ? IAAT_F32 : IAAT_F64;
+                const TileChoice t = choose_tiling(dt, h, w, Keff, -1, true, stage_min_blocks(d, dt, cap));
                 d.variant = (uint8_t)t.variant;
                 d.nbm = (uint8_t)t.nbm;
                 d.nbn = (uint8_t)t.nbn;
