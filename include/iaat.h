@@ -268,7 +268,9 @@ iaat_status_t iaat_pack_destroy(iaat_pack_t pack);
  * (x K) instance of the given type and case with the library's register-tile
  * variants (all four dtypes; complex ones with the complex family) and
  * writes up to `cap` blocks as (row0, col0, rows, cols) quadruples to
- * `blocks`.  Returns the number of blocks (may exceed `cap`),
+ * `blocks`.  This is the per-instance choice; inside a plan, an instance too
+ * large for the staging ring to hold one per consumer warp is given smaller
+ * tiles (more warp blocks), and large instances are first cut into pieces.  Returns the number of blocks (may exceed `cap`),
  * or -1 on bad arguments. */
 int64_t iaat_tile(iaat_dtype_t dtype, int transA, int transB, int M, int N,
                   int K, int32_t *blocks, int64_t cap);
