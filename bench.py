@@ -45,6 +45,9 @@ ROUTE = {"3xbf16-k8ffma": 8}
 # name -> (generator, description, default instances, dtype code, path name, tolerance)
 WORKLOADS = {
     "uneven": ("uneven", WORKLOAD, 200_000, 0, None, 1e-5),
+    "uniform16": ("uniform16", "uniform16-{n}: {n} FP32 NN instances of 16x16x16, ld=16, alpha=1, beta=0.5, "
+                  "U[-1,1], seed 0; the pools fit L2, so launches rotate over five copies of them "
+                  "(5 x 41 MB > 129 MB)", 10_000, 0, None, 1e-5),
     "fc64": ("fc64", "fc64-{n}: {n} FP64 instances, M in {{32,64}}, K,N log-uniform int [8,80], NN/TN 50/50 "
              "(TN redrawn to MNK<=32768), alpha=1, beta in {{0,1}}, U[-1,1], seed 4", 100_000, 1, "dfma", 1e-13),
     "uneven-c32": ("uneven_complex", "uneven-{n}-c32: {n} complex-float instances (CGEMM), M,N,K log-uniform "
@@ -424,7 +427,7 @@ def main():
     # per-variant costs and the stage size of every timed path, measured on
     # this GPU before anything is timed; skipped when a tuning cache is given
     _, wl_desc, _, wl_dtype, wl_path, wl_tol = WORKLOADS[args.workload]
-    if args.workload != "uneven":
+    if args.workload not in ("uneven", "uniform16"):
         # other batches: their type's CUDA-core path alone
         args.precision = wl_path
         args.compare = []
@@ -446,12 +449,20 @@ def main():
         tuned = "built-in cost model (the complex family is not autotuned)"
 
     batch = make_workload(args.workload, args.instances)
-    tA = torch.from_numpy(batch.A).to(dev)
-    tB = torch.from_numpy(batch.B).to(dev)
-    tC = torch.from_numpy(batch.C).to(dev)
+    # a batch that fits in L2 is timed over ROT copies of its pools, one per
+    # launch in turn, so no launch finds its inputs in L2
+    pool_bytes = batch.A.nbytes + batch.B.nbytes + batch.C.nbytes
+    rot = 1 if pool_bytes > 129e6 else int(np.ceil(129e6 / pool_bytes)) + 1
+    tile = (lambda x: x) if rot == 1 else (lambda x: np.tile(x, rot))
+    tA_all = torch.from_numpy(tile(batch.A)).to(dev)
+    tB_all = torch.from_numpy(tile(batch.B)).to(dev)
+    tC_all = torch.from_numpy(tile(batch.C)).to(dev)
+    tA, tB, tC = tA_all[:batch.A.size], tB_all[:batch.B.size], tC_all[:batch.C.size]
     C0 = tC.clone()
     to_descs = iaat.cdescs_for_pools if batch.is_complex else iaat.descs_for_pools
-    descs = to_descs(batch, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
+    descs_rot = [to_descs(batch, tA.data_ptr() + r * batch.A.nbytes, tB.data_ptr() + r * batch.B.nbytes,
+                          tC.data_ptr() + r * batch.C.nbytes) for r in range(rot)]
+    descs = descs_rot[0]
     stream = torch.cuda.Stream(device=dev)
 
     def make_plan(d, name):
@@ -467,8 +478,10 @@ def main():
 
     def time_path(name):
         """First launch (kept for the error check), then a CUDA graph of one
-        launch replayed `steps` times between events on the launch stream."""
-        plan = make_plan(descs, name)
+        launch per pool copy (one launch when the pools exceed L2) replayed
+        between events on the launch stream, `steps` launches in all."""
+        plans = [make_plan(d, name) for d in descs_rot]
+        plan = plans[0]
         info = iaat.iaat_plan_info(plan)
         tC.copy_(C0)
         torch.cuda.synchronize()
@@ -478,9 +491,11 @@ def main():
         first = tC.cpu().numpy() if rank == 0 else None
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            iaat.iaat_gemm_grouped(plan, stream)
+            for p in plans:
+                iaat.iaat_gemm_grouped(p, stream)
+        replays = max(1, args.steps // rot)
         with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
+            for _ in range(max(1, -(-args.warmup // rot))):
                 g.replay()
         torch.cuda.synchronize()
         if world > 1:
@@ -490,14 +505,17 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):   # replay() launches on the current stream
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(replays):
                 g.replay()
             e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        iaat.iaat_plan_check(plan, stream)
+        ms = e0.elapsed_time(e1) / (replays * rot)
+        for p in plans:
+            iaat.iaat_plan_check(p, stream)
+        for p in plans[1:]:
+            p.destroy()
         if world > 1:
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -652,14 +670,16 @@ def main():
                         "roofline_gflops_at_8TBs": roof_gflops,
                         "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None}
         line = {
-            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": max(1, args.steps // rot) * rot,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE_NAMES[wl_dtype], "data": "synthetic",
             "config": {"workload": wl_desc.format(n=batch.count), "instances": batch.count,
                        "precision": args.precision,
                        "parallelism": f"instances x{world} (one batch per GPU)",
-                       "l2": "inputs larger than L2 (pools %.2f GB > 129 MB); no flush" %
-                             ((batch.A.nbytes + batch.B.nbytes + batch.C.nbytes) / 1e9),
+                       "l2": ("inputs larger than L2 (pools %.2f GB > 129 MB); no flush" % (pool_bytes / 1e9))
+                             if rot == 1 else ("pools %.0f MB fit L2: launches rotate over %d copies (%.0f MB); "
+                                               "no flush" % (pool_bytes / 1e6, rot, rot * pool_bytes / 1e6)),
                        "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
                        "grid": info["grid"], "tuning": tuned},
             "roofline": roofline,
@@ -670,7 +690,7 @@ def main():
                     "serial_value": flops * world / (e2e_serial_ms * 1e-3) / 1e9},
             "paths": paths,
             "error": errs.get(args.precision),
-            "gpu_launches": args.steps * info["kernels"],
+            "gpu_launches": max(1, args.steps // rot) * rot * info["kernels"],
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
