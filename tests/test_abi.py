@@ -202,3 +202,38 @@ def test_pack_create_validates_before_the_device(L):
     with pytest.raises(iaat.IaatError) as e:
         iaat.iaat_pack_create(_desc(M=80, N=80, K=81, lda=80, ldb=81, ldc=80), iaat.IAAT_F64)
     assert e.value.status == 2
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The Python mirrors of the header's structs (numpy descriptor dtypes,
+    ctypes option and info structs) have the C compiler's sizes and field
+    offsets."""
+    import ctypes
+    import subprocess
+    fields = {
+        "iaat_gemm_desc_t": (iaat.DESC_DTYPE, [n for n in iaat.DESC_DTYPE.names]),
+        "iaat_cgemm_desc_t": (iaat.CDESC_DTYPE, [n for n in iaat.CDESC_DTYPE.names]),
+    }
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "iaat.h"', 'int main(void) {']
+    for st, (_, names) in fields.items():
+        src.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for n in names:
+            src.append(f'printf("{st}.{n} %zu\\n", offsetof({st}, {n}));')
+    for st, cls in (("iaat_plan_options_t", iaat.PlanOptions), ("iaat_plan_info_t", iaat.PlanInfo)):
+        src.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for n, _ in cls._fields_:
+            src.append(f'printf("{st}.{n} %zu\\n", offsetof({st}, {n}));')
+    src.append('return 0; }')
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", f"-I{os.path.join(ROOT, 'include')}", str(c), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, (dt, names) in fields.items():
+        assert int(got[st]) == dt.itemsize, st
+        for n in names:
+            assert int(got[f"{st}.{n}"]) == dt.fields[n][1], (st, n)
+    for st, cls in (("iaat_plan_options_t", iaat.PlanOptions), ("iaat_plan_info_t", iaat.PlanInfo)):
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for n, _ in cls._fields_:
+            assert int(got[f"{st}.{n}"]) == getattr(cls, n).offset, (st, n)

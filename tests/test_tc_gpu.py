@@ -199,3 +199,39 @@ def test_routed_plan_in_a_graph(cuda):
     iaat.iaat_plan_check(plan, s)
     assert np.array_equal(tC.cpu().numpy().view(np.uint32), first.view(np.uint32))
     plan.destroy()
+
+
+@pytest.mark.parametrize("kmax,route", [(7, 8), (80, 1)])
+def test_routed_plan_with_one_empty_part(kmax, route, cuda):
+    """Every instance routed (K < 8 throughout) or none (route 1): one kernel
+    per call, same values as the path that does the work."""
+    torch = cuda
+    rng = np.random.default_rng(26 + kmax)
+    n = 3000
+    K = rng.integers(1, kmax + 1, n) if kmax < 8 else rng.integers(1, 33, n)
+    M = rng.integers(1, 40, n)
+    N = rng.integers(1, 40, n)
+    b = W.make_batch(M, N, K, rng.integers(0, 2, n), rng.integers(0, 2, n), rng.uniform(-2, 2, n),
+                     rng.uniform(-2, 2, n), np.float32, rng, pad=rng.integers(0, 4, (n, 3)))
+    b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])
+    C, info = run_grouped(b, iaat.IAAT_PREC_3XBF16, route_k_below=route)
+    assert info["kernels"] == 1
+    err = compare(b, C)
+    assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= (1e-5 if kmax < 8 else 1e-4), err
+    ref, _ = run_grouped(b, iaat.IAAT_PREC_DEFAULT if kmax < 8 else iaat.IAAT_PREC_3XBF16)
+    assert np.array_equal(C.view(np.uint32), ref.view(np.uint32))
+
+
+def test_empty_plans(cuda):
+    """Zero instances: every plan kind builds, launches nothing and checks clean."""
+    torch = cuda
+    s = torch.cuda.current_stream()
+    for make in (lambda: iaat.iaat_plan_create(np.zeros(0, iaat.DESC_DTYPE), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16,
+                                               route_k_below=8),
+                 lambda: iaat.iaat_plan_create_complex(np.zeros(0, iaat.CDESC_DTYPE), iaat.IAAT_C64)):
+        plan = make()
+        iaat.iaat_gemm_grouped(plan, s)
+        iaat.iaat_plan_check(plan, s)
+        info = iaat.iaat_plan_info(plan)
+        assert info["instances"] == 0 and info["flops"] == 0
+        plan.destroy()
