@@ -167,6 +167,28 @@ iaat_status_t iaat_dgemm(int transA, int transB, int M, int N, int K,
                          const double *B, int ldb, double beta, double *C,
                          int ldc, void *stream);
 
+/* Single small complex GEMM, CGEMM (complex float) / ZGEMM (complex double),
+ * Table I rows 3-4: the operation, cases and argument rules of
+ * iaat_cgemm_desc_t with one instance.  alpha and beta point to (re, im)
+ * pairs in host memory, read during the call; A, B, C are device pointers
+ * aligned to 8 (CGEMM) or 16 (ZGEMM) bytes.  Asynchronous on `stream`, no
+ * allocation: the call plans on the host and copies the instance's scalars
+ * and stage programs into one fixed device scratch array of 512 KB (a
+ * file-scope __device__ array every GPU loading this library holds), then
+ * launches the complex kernel, its C cut into pieces of about 16 x 16
+ * (ZGEMM) or 32 x 32 (CGEMM) that run on separate SMs.  Calls reuse that
+ * scratch, so calls that overlap on the GPU (other streams or threads) race:
+ * order them on one stream.  A device time-out is reported by
+ * iaat_plan_check(NULL, stream).  Batches: iaat_plan_create_complex. */
+iaat_status_t iaat_cgemm(int transA, int transB, int M, int N, int K,
+                         const float *alpha, const void *A, int lda,
+                         const void *B, int ldb, const float *beta, void *C,
+                         int ldc, void *stream);
+iaat_status_t iaat_zgemm(int transA, int transB, int M, int N, int K,
+                         const double *alpha, const void *A, int lda,
+                         const void *B, int ldb, const double *beta, void *C,
+                         int ldc, void *stream);
+
 /* Allocation-free grouped GEMM.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory after start-up
  * -- for example a serving process that reserves all GPU memory at launch and

@@ -1124,6 +1124,119 @@ extern "C" iaat_status_t iaat_dgemm(int transA, int transB, int M, int N, int K,
     return single_gemm(8, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
 }
 
+// ------------------------------------------- single complex GEMM call
+// One CGEMM / ZGEMM instance per call.  Complex tasks carry their scalars in
+// a table, so these calls plan on the host like a plan does, but into the
+// kernel's fixed single-call scratch (no allocation): the instance is cut
+// into pieces of about piece x piece of C, each its own stage, so that the
+// pieces run on as many SMs (one SM's DFMA rate would otherwise set the
+// latency), and the scalars, program offsets and stage programs are copied
+// into the scratch on the caller's stream before the launch.
+static std::mutex g_cplx_single_mutex;
+constexpr int kCplxSinglePieces = 152;   // pieces (stages) of one call at most, before pieces grow
+
+static iaat_status_t single_complex(int dt, int ta, int tb, int M, int N, int K, const double *alpha, const void *A,
+                                    int lda, const void *B, int ldb, const double *beta, void *C, int ldc, void *stream)
+{
+    const int esz = dtype_esz(dt);
+    if (!alpha || !beta)
+        return fail(IAAT_ERR_INVALID_VALUE, "alpha or beta is NULL");
+    double v[4] = {alpha[0], alpha[1], beta[0], beta[1]};
+    if (dt == IAAT_C32)
+        for (double &x : v)
+            x = (double)(float)x;
+    const double am = (v[0] != 0.0 || v[1] != 0.0) ? 1.0 : 0.0;
+    const double bm = (v[2] == 0.0 && v[3] == 0.0) ? 0.0 : (v[2] == 1.0 && v[3] == 0.0) ? 1.0 : 2.0;
+    iaat_status_t st = check_instance(0, M, N, K, lda, ldb, ldc, ta, tb, A, B, C, am, esz);
+    if (st != IAAT_OK)
+        return st;
+    iaat_gemm_desc_t g{M, N, K, lda, ldb, ldc, ta, tb, am, bm, A, B, C};
+    const uint32_t cap = (uint32_t)cplx_max_group_bytes();
+    int piece = dt == IAAT_C64 ? 16 : 32;
+    while (piece < kPieceRows && (int64_t)((M + piece - 1) / piece) * ((N + piece - 1) / piece) > kCplxSinglePieces)
+        piece *= 2;
+    std::vector<HostTask> tasks;
+    int64_t nb = 0;
+    st = make_tasks(0, g, dt, false, -1, cap, tasks, &nb, piece);
+    if (st != IAAT_OK)
+        return st;
+    if (tasks.empty())
+        return IAAT_OK;
+    std::vector<TaskDesc> flat;
+    std::vector<int32_t> gbeg;
+    make_groups(tasks, cap, 1, flat, gbeg);   // one piece per stage
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    st = prepare_device(dev, kernel_kind(dt, IAAT_PREC_DEFAULT));
+    if (st != IAAT_OK)
+        return st;
+    const int ng = (int)gbeg.size() - 1;
+    const int grid = std::min(ng, sm_count(dev));
+    std::lock_guard<std::mutex> lk(g_cplx_single_mutex);
+    char *scr = nullptr;
+    size_t scr_bytes = 0;
+    if ((e = cplx_single_scratch(&scr, &scr_bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress of the single-call scratch");
+    uint32_t ring_off = 0, ring_bytes = 0;
+    cplx_ring(&ring_off, &ring_bytes);
+    std::vector<char> prog;
+    std::vector<int64_t> poff;
+    const uint32_t stride = (uint32_t)(2 * esz);
+    st = build_programs(flat, gbeg, std::vector<PackInfo>(), std::vector<int32_t>(), esz, false, grid, ring_off,
+                        ring_bytes, scr, stride, prog, poff);
+    if (st != IAAT_OK)
+        return st;
+    const size_t poff_at = 256, prog_at = poff_at + ((poff.size() * sizeof(int64_t) + 255) & ~(size_t)255);
+    if (prog_at + prog.size() > scr_bytes)
+        return fail(IAAT_ERR_UNSUPPORTED, "the call's stage programs (%zu bytes) exceed the single-call scratch",
+                    prog.size());
+    char sc[32];
+    for (int c = 0; c < 4; ++c) {
+        if (dt == IAAT_C32) {
+            const float f = (float)v[c];
+            std::memcpy(sc + 4 * c, &f, 4);
+        } else {
+            std::memcpy(sc + 8 * c, &v[c], 8);
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // pageable sources: each copy has taken its bytes when it returns
+    if ((e = cudaMemcpyAsync(scr, sc, stride, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(scr + poff_at, poff.data(), poff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(scr + prog_at, prog.data(), prog.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy into the single-call scratch");
+    KParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.p.prog = scr + prog_at;
+    kp.p.poff = reinterpret_cast<const int64_t *>(scr + poff_at);
+    kp.p.ngroups = (int32_t)ng;
+    int32_t *w = nullptr;
+    if ((e = single_call_err_ptr(&w)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress");
+    kp.p.err = w;
+    if ((e = launch_cplx(dt, kp, grid, s)) != cudaSuccess)
+        return cuda_fail(e, "kernel launch");
+    return IAAT_OK;
+}
+
+extern "C" iaat_status_t iaat_cgemm(int transA, int transB, int M, int N, int K, const float *alpha, const void *A,
+                                    int lda, const void *B, int ldb, const float *beta, void *C, int ldc, void *stream)
+{
+    if (!alpha || !beta)
+        return fail(IAAT_ERR_INVALID_VALUE, "alpha or beta is NULL");
+    const double a[2] = {alpha[0], alpha[1]}, b[2] = {beta[0], beta[1]};
+    return single_complex(IAAT_C32, transA, transB, M, N, K, a, A, lda, B, ldb, b, C, ldc, stream);
+}
+
+extern "C" iaat_status_t iaat_zgemm(int transA, int transB, int M, int N, int K, const double *alpha, const void *A,
+                                    int lda, const void *B, int ldb, const double *beta, void *C, int ldc, void *stream)
+{
+    return single_complex(IAAT_C64, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
 extern "C" iaat_status_t iaat_fma_peak(iaat_dtype_t dtype, double *gflops)
 {
     if ((dtype != IAAT_F32 && dtype != IAAT_F64) || !gflops)

@@ -37,4 +37,16 @@ void cplx_ring(uint32_t *off, uint32_t *bytes)
     *bytes = (uint32_t)cplx_ring_bytes();
 }
 
+// Scratch of the single-call complex entry points (iaat_cgemm / iaat_zgemm):
+// the call's scalars, stage-program offsets and stage programs, in a fixed
+// array that every GPU loading this library holds (512 KB).
+constexpr size_t kCplxSingleBytes = 512 * 1024;
+static __device__ __align__(256) unsigned char g_cplx_single[kCplxSingleBytes];
+
+cudaError_t cplx_single_scratch(char **p, size_t *bytes)
+{
+    *bytes = kCplxSingleBytes;
+    return cudaGetSymbolAddress(reinterpret_cast<void **>(p), g_cplx_single);
+}
+
 }  // namespace iaat

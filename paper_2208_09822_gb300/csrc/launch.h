@@ -20,6 +20,7 @@ cudaError_t launch_cplx(int dtype, const KParams &kp, int grid, cudaStream_t str
 void fma_ring(int esz, uint32_t *off, uint32_t *bytes);
 void tc_ring(int precision, uint32_t *off, uint32_t *bytes);
 void cplx_ring(uint32_t *off, uint32_t *bytes);
+cudaError_t cplx_single_scratch(char **p, size_t *bytes);   // device scratch of iaat_cgemm / iaat_zgemm
 constexpr int kTcPackRows = 128;        // rows of one MMA tile
 constexpr int kTcPackCols = 128;        // columns of one MMA tile
 // Allocation-free planning into caller-supplied arrays (host.cpp); used by

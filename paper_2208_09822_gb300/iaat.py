@@ -72,6 +72,10 @@ def lib():
         L.iaat_sgemm.argtypes = [I, I, I, I, I, F, P, I, P, I, F, P, I, P]
         L.iaat_dgemm.restype = S
         L.iaat_dgemm.argtypes = [I, I, I, I, I, D, P, I, P, I, D, P, I, P]
+        L.iaat_cgemm.restype = S
+        L.iaat_cgemm.argtypes = [I, I, I, I, I, ctypes.POINTER(F), P, I, P, I, ctypes.POINTER(F), P, I, P]
+        L.iaat_zgemm.restype = S
+        L.iaat_zgemm.argtypes = [I, I, I, I, I, ctypes.POINTER(D), P, I, P, I, ctypes.POINTER(D), P, I, P]
         L.iaat_plan_create.restype = S
         L.iaat_plan_create.argtypes = [P, ctypes.c_int64, I, I, ctypes.POINTER(PlanOptions),
                                        ctypes.POINTER(ctypes.c_void_p)]
@@ -138,6 +142,20 @@ def iaat_sgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, str
 
 def iaat_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
     _check(lib().iaat_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, _stream(stream)))
+
+
+def iaat_cgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """Single complex-float GEMM; alpha and beta are Python complex numbers."""
+    al = (ctypes.c_float * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_float * 2)(complex(beta).real, complex(beta).imag)
+    _check(lib().iaat_cgemm(transA, transB, M, N, K, al, A, lda, B, ldb, be, C, ldc, _stream(stream)))
+
+
+def iaat_zgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """Single complex-double GEMM; alpha and beta are Python complex numbers."""
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    _check(lib().iaat_zgemm(transA, transB, M, N, K, al, A, lda, B, ldb, be, C, ldc, _stream(stream)))
 
 
 class Plan:

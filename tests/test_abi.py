@@ -237,3 +237,19 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for n, _ in cls._fields_:
             assert int(got[f"{st}.{n}"]) == getattr(cls, n).offset, (st, n)
+
+
+def test_single_complex_calls_reject_before_the_device(L):
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_zgemm(0, 0, 81, 80, 80, 1.0, 0x1000, 81, 0x2000, 80, 0.0, 0x3000, 81)
+    assert e.value.status == 2
+    with pytest.raises(iaat.IaatError) as e:   # 8 bytes past 16: aligned for CGEMM, not ZGEMM
+        iaat.iaat_zgemm(0, 0, 4, 4, 4, 1.0, 0x1008, 4, 0x2000, 4, 0.0, 0x3000, 4)
+    assert e.value.status == 3
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_cgemm(1, 0, 32, 32, 33, 1j, 0x1000, 33, 0x2000, 33, 0.0, 0x3000, 32)
+    assert e.value.status == 2
+    assert iaat.lib().iaat_cgemm(0, 0, 4, 4, 4, None, 0x1000, 4, 0x2000, 4, None, 0x3000, 4, None) == 1
+    # quick returns touch nothing
+    iaat.iaat_cgemm(0, 0, 0, 5, 5, 1.0, 0, 1, 0, 5, 0.0, 0, 1)
+    iaat.iaat_zgemm(0, 0, 5, 5, 5, 0.0, 0, 5, 0, 5, 1.0, 0x3000, 5)

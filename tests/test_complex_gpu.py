@@ -167,3 +167,33 @@ def test_corrupt_program_is_reported(cuda):
         iaat.iaat_plan_check(plan, s)
     assert e.value.status == 6
     plan.destroy()
+
+
+@pytest.mark.parametrize("dtype", CTYPES)
+def test_single_calls(dtype, cuda):
+    """iaat_cgemm / iaat_zgemm, one instance per call on one stream, over
+    every case and sizes up to the domain's edges (80^3, 1 x 6400 x 80)."""
+    torch = cuda
+    rng = np.random.default_rng(42)
+    shapes = [(1, 1, 1), (3, 5, 2), (16, 16, 16), (33, 17, 9), (80, 80, 80), (1, 6400, 80), (64, 1, 80),
+              (32, 32, 32), (20, 30, 0)]
+    M, N, K, ta, tb = [], [], [], [], []
+    for (m, n, k) in shapes:
+        for t in range(4):
+            a, b_ = t >> 1, t & 1
+            if W.in_domain(m, n, k, a, b_):
+                M.append(m); N.append(n); K.append(k); ta.append(a); tb.append(b_)
+    n_ = len(M)
+    alpha = rng.uniform(-2, 2, n_) + 1j * rng.uniform(-2, 2, n_)
+    beta = rng.uniform(-2, 2, n_) + 1j * rng.uniform(-2, 2, n_)
+    beta[::5] = 0
+    b = W.make_batch(M, N, K, ta, tb, alpha, beta, dtype, rng, pad=rng.integers(0, 3, (n_, 3)))
+    tA, tB, tC, descs = to_device(b)
+    s = torch.cuda.current_stream()
+    call = iaat.iaat_cgemm if dtype == np.complex64 else iaat.iaat_zgemm
+    for d, al, be in zip(descs, b.alpha, b.beta):
+        call(int(d["transA"]), int(d["transB"]), int(d["M"]), int(d["N"]), int(d["K"]), complex(al), int(d["A"]),
+             int(d["lda"]), int(d["B"]), int(d["ldb"]), complex(be), int(d["C"]), int(d["ldc"]), s)
+    iaat.iaat_plan_check(None, s)
+    C = tC.cpu().numpy()
+    _assert_ok(b, C, compare(b, C), TOL[dtype])
