@@ -454,7 +454,12 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc
                 d.alpha = (double)idx;
                 d.beta = 0.0;
             }
-            const int min_blocks = (!tc && piece == 0 && force_variant < 0) ? stage_min_blocks(d, dt, cap) : 1;
+            // a single call's pieces run one per CTA: give each enough warp
+            // blocks for the consumer warps (DFMA-bound pieces use every
+            // sub-partition's pipe that way)
+            const int min_blocks = (tc || force_variant >= 0) ? 1
+                                   : piece > 0                 ? fma_warps(dt)
+                                                               : stage_min_blocks(d, dt, cap);
             const TileChoice t = choose_tiling(dt, h, w, Keff, force_variant, !tc, min_blocks);
             d.variant = (uint8_t)t.variant;
             d.nbm = (uint8_t)t.nbm;
