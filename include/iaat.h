@@ -307,7 +307,7 @@ int64_t iaat_tile_exact(int M, int N, const int32_t *heights,
                         const int32_t *max_width, int nheights,
                         int32_t *blocks, int64_t cap, int64_t *sum_out);
 
-/* Version string of this build. */
+/* Version string of the library. */
 const char *iaat_version(void);
 
 /* Message for the calling thread's last failing call ("" if none). */

@@ -132,7 +132,7 @@ int oracle_gemm_batch(int64_t count, int is_f64,
     return 0;
 }
 
-/* Number of threads an OpenMP region of this build uses (1 without OpenMP). */
+/* Number of threads an OpenMP region of the compiled oracle uses (1 without OpenMP). */
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
