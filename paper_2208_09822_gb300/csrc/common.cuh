@@ -193,14 +193,22 @@ constexpr Variant kVariantsF32[kNumVariantsF32] = {
     {1, 2, 8, 4},   // 4: 8 x 8
 };
 
-// FP64 family (DFMA; each accumulator takes two registers).
-constexpr int kNumVariantsF64 = 5;
+// FP64 family (DFMA; each accumulator takes two registers).  DFMA-bound
+// work pays a DFMA slot for every idle lane of a partly filled tile, so the
+// family adds narrow tiles (32 x 8 down to 32 x 1, and 8 x 4) for
+// instances whose width is not a multiple of 16.
+constexpr int kNumVariantsF64 = 10;
 constexpr Variant kVariantsF64[kNumVariantsF64] = {
-    {4, 8, 8, 4},   // 0: 32 x 32
-    {4, 4, 8, 4},   // 1: 32 x 16
-    {4, 4, 4, 8},   // 2: 16 x 32
-    {2, 4, 8, 4},   // 3: 16 x 16
-    {1, 2, 8, 4},   // 4: 8 x 8
+    {4, 8, 8, 4},    // 0: 32 x 32
+    {4, 4, 8, 4},    // 1: 32 x 16
+    {4, 4, 4, 8},    // 2: 16 x 32
+    {2, 4, 8, 4},    // 3: 16 x 16
+    {1, 2, 8, 4},    // 4: 8 x 8
+    {4, 2, 8, 4},    // 5: 32 x 8
+    {4, 1, 8, 4},    // 6: 32 x 4
+    {2, 1, 16, 2},   // 7: 32 x 2
+    {1, 1, 32, 1},   // 8: 32 x 1
+    {1, 1, 8, 4},    // 9: 8 x 4
 };
 
 // Complex families (CGEMM / ZGEMM, Table I rows 3-4): an accumulator is a

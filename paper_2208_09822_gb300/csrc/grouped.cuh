@@ -741,7 +741,7 @@ __device__ __forceinline__ void dispatch_block<double>(const char *smem, const T
             smem, r, bi, bj, As, Bs);                                                                 \
         break;
     switch (r.variant) {
-        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4)
+        IAAT_V(0) IAAT_V(1) IAAT_V(2) IAAT_V(3) IAAT_V(4) IAAT_V(5) IAAT_V(6) IAAT_V(7) IAAT_V(8) IAAT_V(9)
     default:
         break;
     }

@@ -180,7 +180,7 @@ def test_every_fp32_variant(variant):
     _assert_ok(b, C, compare(b, C), 1e-5)
 
 
-@pytest.mark.parametrize("variant", range(1, 6))
+@pytest.mark.parametrize("variant", range(1, 11))
 def test_every_fp64_variant(variant):
     b = W.random_small(400, seed=200 + variant, dtype=np.float64, max_dim=70, pad_max=4, misalign_max=1)
     b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])
