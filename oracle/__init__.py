@@ -10,6 +10,8 @@ the GEMM arithmetic.
   transposition names and column-major storage) as an FP64 triple loop, for
   real and for complex (CGEMM/ZGEMM, Table I rows 3-4) batches.
 * ``tiler_oracle.py`` -- Algorithm 2 (Sec. V-A) and the memops count.
+* ``split_oracle.py`` -- the steps of the tensor-core paths (operand
+  rounding to BF16 terms, TF32 or FP16, and their product sets) in FP64.
 """
 from __future__ import annotations
 
