@@ -37,6 +37,12 @@ WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT
             "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
 NOMINAL_HBM_GBS = 8000.0
 PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4, "3xbf16-k8ffma": 1}
+# each path can also be forced onto one kernel family: name + "@stage"
+# (stage-program kernels) or name + "@stream" (warp-stream / pack-stream)
+for _n in list(PRECISIONS):
+    PRECISIONS[_n + "@stage"] = PRECISIONS[_n + "@stream"] = PRECISIONS[_n]
+KERNEL = {n: (1 if n.endswith("@stage") else 2 if n.endswith("@stream") else 0) for n in PRECISIONS}
+ROUTE_BASE = lambda n: n.split("@")[0]
 # paths that route small-K instances to the FP32 CUDA-core kernel (route_k_below)
 ROUTE = {"3xbf16-k8ffma": 8}
 
@@ -467,7 +473,8 @@ def main():
 
     def make_plan(d, name):
         if wl_dtype == 0:
-            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name], route_k_below=ROUTE.get(name, 0))
+            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name],
+                                         route_k_below=ROUTE.get(ROUTE_BASE(name), 0), kernel=KERNEL.get(name, 0))
         if wl_dtype == 1:
             return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
         return iaat.iaat_plan_create_complex(d, wl_dtype)

@@ -131,7 +131,15 @@ typedef struct {
                                   the same stream).  The split's dropped low-low term
                                   is not averaged out at tiny K; with 8, every
                                   instance meets FP32-like accuracy.  0: no routing */
-    int32_t reserved[3];
+    int32_t kernel;            /* FP32 plans: 0 = default, 1 = the stage-program kernels
+                                  (one producer warp per SM fills pipeline stages that
+                                  all compute warps share), 2 = the stream kernels (the
+                                  CUDA-core warp-stream kernel, in which every warp
+                                  streams its own warp tasks, and the tensor-core
+                                  pack-stream kernel, in which four warp groups with a
+                                  producer warp each stream dense 128-row packs).
+                                  FP64 and complex plans always run stage programs */
+    int32_t reserved[2];
 } iaat_plan_options_t;
 
 /* Statistics of a plan (iaat_plan_info). */

@@ -341,6 +341,100 @@ struct KParams {
 };
 static_assert(sizeof(KParams) <= 4096, "kernel parameter block");
 
+// ------------------------------------------------ warp-stream kernel
+// (ws.cuh) The FP32 CUDA-core plans run a kernel in which every warp streams
+// its own list of warp tasks through a private shared-memory ring.
+// One warp task.  64 bytes; the first 64 bytes of every ring item are a copy.
+struct alignas(16) WsTask {
+    const char *A;        // op(A) element (r0, 0) of the block in the stored A
+    const char *B;        // op(B) element (0, c0) of the block in the stored B
+    char *C;              // C element (r0, c0)
+    int32_t lda, ldb, ldc;
+    int32_t K;            // K (0: no product); streamed in chunks, so any K of the domain
+    int16_t M, N;         // block rows, block columns
+    uint8_t ta, tb, variant, flags;
+    float alpha, beta;
+    int32_t pad[2];
+};
+static_assert(sizeof(WsTask) == 64, "WsTask layout");
+
+struct WsParams {
+    const WsTask *tasks;   // warp w's tasks: tasks[wbeg[w] .. wbeg[w+1])
+    const int32_t *wbeg;
+    int32_t *err;
+    int32_t nwarps;        // gridDim.x * kWsWarps
+    int32_t pad;
+};
+
+constexpr int kWsWarps = 16;                 // warps per CTA, one CTA per SM
+constexpr int kWsKC = 16;                    // K values per item
+constexpr int kWsMaxOut = 8;                 // items in flight per warp
+constexpr int kWsHdr = 80;                   // item header: task record + 16 bytes of chunk info
+constexpr int kWsCStride = 32;               // column stride (floats) of the staged C block
+constexpr int kWsRingBytes = (kSmemTotal / kWsWarps) & ~127;   // 14464 bytes per warp
+constexpr int kWsMaxItem = kWsHdr + 2 * kWsKC * 32 * 4 + kWsCStride * 32 * 4;
+static_assert(kWsMaxItem <= kWsRingBytes, "one item of the largest tile must fit the ring");
+constexpr int kWsThreads = 32 * kWsWarps;
+
+// ------------------------------------------- pack-stream tensor-core kernel
+// (tc2.cuh) Tensor-core plans run a kernel with four independent groups of
+// four warps per SM; each group streams its own list of packs (one 128-row
+// MMA tile of up to kT2MaxTasks tasks).  A pack's program in global memory is
+//   Tc2Hdr | Tc2Rec[ntasks] | (unused record slots) | CopyCmd[ncmd]
+// (16-byte aligned), the commands always kT2CmdOff bytes after the header so
+// that one fixed window holds the header, the records and the first
+// commands; the header and records are copied to the start of the pack's
+// staging item, the commands bring the raw operands after them.
+struct alignas(16) Tc2Hdr {
+    int32_t ntasks;       // tasks of the pack (1..kT2MaxTasks)
+    int32_t ncmd;         // copy commands
+    int32_t kpack;        // MMA K: the largest K of the pack, rounded up to the MMA K step (0: no product)
+    int32_t nt;           // MMA N: the end of the last task's columns, a multiple of 16 (16..kT2Cols)
+    uint32_t item_bytes;  // staging bytes of the pack (multiple of 16)
+    uint32_t rec_bytes;   // header + records (copied first)
+    uint32_t tx_bytes;    // bytes all copies of the pack deliver, records included
+    int32_t pad0;
+    int64_t next[2];      // programs of the next two packs of the same warp group (-1: none)
+    int32_t pad1[4];
+};
+static_assert(sizeof(Tc2Hdr) == 64, "Tc2Hdr layout");
+
+// One task of a pack: element (r, c) of its stored X sits at item + offX +
+// c*csX + r*4 in the staging item.  Its rows are rows row0.. of the MMA tile
+// (tensor-memory lanes) and its columns columns col0.. of the accumulator.
+struct alignas(16) Tc2Rec {
+    char *C;
+    int32_t ldc;
+    int32_t offA, offB, offC;
+    int32_t csA, csB, csC;
+    int32_t K;
+    int16_t M, N;
+    uint8_t ta, tb, row0, col0;
+    uint8_t flags, pad0;
+    int16_t pad1;
+    float alpha, beta;
+};
+static_assert(sizeof(Tc2Rec) == 64, "Tc2Rec layout");
+
+struct Tc2Params {
+    const char *prog;        // pack programs
+    const int64_t *poff;     // program of pack p at prog + poff[p]
+    const int32_t *gbeg;     // group gg runs packs [gbeg[gg], gbeg[gg+1])
+    int32_t *err;
+    int32_t ngroups;         // gridDim.x * kT2Groups
+    int32_t pad;
+};
+
+constexpr int kT2Groups = 4;              // warp groups per CTA (one CTA per SM)
+constexpr int kT2Threads = 32 * 5 * kT2Groups;   // per group four warps and a producer warp
+constexpr int kT2KC = 16;                 // K values per converted operand chunk
+constexpr int kT2Inflight = 4;            // packs in flight per group
+constexpr int kT2Cols = 128;              // accumulator columns of a group
+constexpr int kT2MaxTasks = 8;            // tasks per pack
+constexpr int kT2CmdOff = 64 + kT2MaxTasks * 64;           // byte offset of the commands in a program
+constexpr int kT2WinCmds = 64;                             // commands in the prefetched window
+constexpr int kT2Window = kT2CmdOff + kT2WinCmds * 16;     // bytes of a program the issuing warp prefetches
+
 constexpr int32_t kErrTimeoutFull = 1;
 constexpr int32_t kErrTimeoutEmpty = 2;
 constexpr int32_t kErrBadGroup = 4;

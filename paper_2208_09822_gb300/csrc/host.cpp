@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <queue>
 #include <vector>
 
 #include "../../include/iaat.h"
@@ -276,6 +277,12 @@ struct iaat_plan_s {
     int32_t *d_err = nullptr;
     char *d_scal = nullptr;        // complex plans: alpha, beta of every instance
     iaat_plan_s *sub = nullptr;    // routed plans: the FP32 CUDA-core plan of the small-K instances
+    bool tc2 = false;              // pack-stream tensor-core kernel
+    int32_t *d_gbeg = nullptr;     // its packs per warp group
+    Tc2Params t2p{};
+    bool ws = false;               // warp-stream kernel (FP32 CUDA-core plans)
+    char *d_ws = nullptr;          // its warp tasks, per-warp ranges and error word
+    WsParams wsp{};
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
     iaat_plan_info_t info{};
@@ -290,19 +297,22 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][8];
+bool g_prepared[64][13];
 
-// kind: 0 = FP32 FFMA, 1 = FP64 DFMA, 2..5 = tcgen05 precision (kind - 1),
-// 6 = complex float, 7 = complex double
+// kind: 0 = FP32 FFMA (stage programs), 1 = FP64 DFMA, 2..5 = tcgen05
+// precision (kind - 1), 6 = complex float, 7 = complex double, 8 = FP32 FFMA
+// warp-stream kernel, 9..12 = pack-stream tensor-core kernel, precision kind - 8
 iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
     if (dev < 0 || dev >= 64)
         return fail(IAAT_ERR_CUDA, "device index %d out of range", dev);
     if (!g_prepared[dev][kind]) {
-        cudaError_t e = kind < 2   ? prepare_fma(kind)
-                        : kind < 6 ? prepare_tc(kind - 1)
-                                   : prepare_cplx(kind == 6 ? IAAT_C32 : IAAT_C64);
+        cudaError_t e = kind < 2    ? prepare_fma(kind)
+                        : kind < 6  ? prepare_tc(kind - 1)
+                        : kind == 8 ? prepare_ws()
+                        : kind > 8  ? prepare_tc2(kind - 8)
+                                    : prepare_cplx(kind == 6 ? IAAT_C32 : IAAT_C64);
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaFuncSetAttribute");
         g_prepared[dev][kind] = true;
@@ -698,6 +708,601 @@ iaat_status_t build_programs(const std::vector<TaskDesc> &flat, const std::vecto
 
 }  // namespace
 
+// ------------------------------------------------ warp-stream planner
+// FP32 CUDA-core plans run the warp-stream kernel (ws.cuh): every instance
+// is cut into warp tasks (one warp block of C each, the whole K), and the
+// tasks are dealt to the warps of the grid ahead of time.
+
+// Warp instructions that copy a region of Y lines of L elements each (one
+// 4-byte cp.async per element, floor(32 / L) lines per instruction).
+static double ws_copy_instr(int L, int Y)
+{
+    if (L <= 0 || Y <= 0)
+        return 0.0;
+    const int step = 32 / std::min(L, 32);
+    return (double)((Y + step - 1) / step);
+}
+
+// Issue slots of one warp task: per K-chunk the rank-1 updates (FMAs and
+// 16-byte shared loads), the copies of op(A) and op(B) (about six issue
+// slots per copy instruction with its address arithmetic) and a fixed cost;
+// then the copy of C0, the epilogue and a fixed cost per task.
+constexpr double kWsCopySlots = 6.0, kWsChunkSlots = 60.0, kWsTaskSlots = 80.0;
+
+static double ws_task_cost(const Variant &v, int mh, int nw, int K, int ta, int tb, bool readc)
+{
+    double c = kWsTaskSlots;
+    const double lds = (v.mr >= 4 ? v.mr / 4 : v.mr) + (v.nr >= 4 ? v.nr / 4 : v.nr);
+    for (int k0 = 0; k0 < K; k0 += kWsKC) {
+        const int kc = std::min(kWsKC, K - k0), kcp = (kc + 3) & ~3;
+        c += kcp * (v.mr * v.nr + lds) + kWsChunkSlots;
+        c += kWsCopySlots * ((ta ? ws_copy_instr(kc, mh) : ws_copy_instr(mh, kc)) +
+                             (tb ? ws_copy_instr(nw, kc) : ws_copy_instr(kc, nw)));
+    }
+    if (K == 0)
+        c += kWsChunkSlots;
+    if (readc)
+        c += kWsCopySlots * ws_copy_instr(mh, nw);
+    return c + 3.0 * v.mr * v.nr + 6.0 * ((mh * nw + 31) / 32);
+}
+
+// Cost of tiling an M x N (x K) instance with variant v: its rows cut into
+// ceil(M / bm) near-equal block heights and its columns likewise.
+static double ws_tiling_cost(const Variant &v, int M, int N, int K, int ta, int tb, bool readc, int64_t *nblocks)
+{
+    const int bm = v.lm * v.mr, bn = v.ln * v.nr;
+    const int nbm = (M + bm - 1) / bm, nbn = (N + bn - 1) / bn;
+    *nblocks = (int64_t)nbm * nbn;
+    // near-equal split: M % nbm blocks of ceil(M / nbm) rows, the rest floor
+    const int hr = M / nbm, wr = N / nbn;
+    const int64_t nh1 = M % nbm, nh0 = nbm - nh1, nw1 = N % nbn, nw0 = nbn - nw1;
+    double c = 0.0;
+    if (nh0 && nw0) c += (double)(nh0 * nw0) * ws_task_cost(v, hr, wr, K, ta, tb, readc);
+    if (nh0 && nw1) c += (double)(nh0 * nw1) * ws_task_cost(v, hr, wr + 1, K, ta, tb, readc);
+    if (nh1 && nw0) c += (double)(nh1 * nw0) * ws_task_cost(v, hr + 1, wr, K, ta, tb, readc);
+    if (nh1 && nw1) c += (double)(nh1 * nw1) * ws_task_cost(v, hr + 1, wr + 1, K, ta, tb, readc);
+    return c;
+}
+
+// Weight of one byte of HBM traffic in the assignment cost, in issue slots:
+// at the HBM roof an SM moves about 45 GB/s while it issues about 8,300
+// warp instructions per microsecond, so one byte is worth about 0.19 slots.
+constexpr double kWsByteSlots = 0.19;
+
+static iaat_status_t plan_create_ws(const iaat_gemm_desc_t *descs, int64_t count, const iaat_plan_options_t *opts,
+                                    int force_variant, iaat_plan_t *out, const int64_t *index_map)
+{
+    std::vector<WsTask> tasks;
+    std::vector<double> cost;
+    tasks.reserve((size_t)count * 2);
+    cost.reserve((size_t)count * 2);
+    iaat_plan_info_t info{};
+    info.instances = count;
+    info.dtype = IAAT_F32;
+    info.precision = IAAT_PREC_DEFAULT;
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        const int64_t gi = index_map ? index_map[i] : i;
+        iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+                                          g.alpha, 4);
+        if (st != IAAT_OK)
+            return st;
+        const int M = g.M, N = g.N;
+        if (M == 0 || N == 0)
+            continue;
+        const int K = (g.alpha == 0.0) ? 0 : g.K;
+        if (K == 0 && g.beta == 1.0)
+            continue;   // C = 1*C: nothing to do
+        const bool readc = g.beta != 0.0;
+        info.active += 1;
+        info.flops += 2 * (int64_t)M * N * K;
+        info.algorithmic_bytes += ((int64_t)M * K + (int64_t)K * N + (int64_t)M * N + (readc ? (int64_t)M * N : 0)) * 4;
+        int best = 0;
+        double best_cost = 1e300;
+        for (int v = 0; v < kNumVariantsF32; ++v) {
+            if (force_variant >= 0 && v != force_variant)
+                continue;
+            int64_t nb = 0;
+            const double c = ws_tiling_cost(kVariantsF32[v], M, N, K, g.transA, g.transB, readc, &nb);
+            if (c < best_cost) {
+                best_cost = c;
+                best = v;
+            }
+        }
+        const Variant &vv = kVariantsF32[best];
+        const int bm = vv.lm * vv.mr, bn = vv.ln * vv.nr;
+        const int nbm = (M + bm - 1) / bm, nbn = (N + bn - 1) / bn;
+        for (int bj = 0; bj < nbn; ++bj) {
+            int c0, nw;
+            piece_range(N, nbn, bj, c0, nw);
+            for (int bi = 0; bi < nbm; ++bi) {
+                int r0, mh;
+                piece_range(M, nbm, bi, r0, mh);
+                WsTask t{};
+                if (K > 0) {
+                    t.A = static_cast<const char *>(g.A) + (size_t)(g.transA ? (int64_t)r0 * g.lda : (int64_t)r0) * 4;
+                    t.B = static_cast<const char *>(g.B) + (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * 4;
+                }
+                t.C = static_cast<char *>(g.C) + (size_t)((int64_t)r0 + (int64_t)c0 * g.ldc) * 4;
+                t.lda = g.lda;
+                t.ldb = g.ldb;
+                t.ldc = g.ldc;
+                t.M = (int16_t)mh;
+                t.N = (int16_t)nw;
+                t.K = K;
+                t.ta = (uint8_t)g.transA;
+                t.tb = (uint8_t)g.transB;
+                t.variant = (uint8_t)best;
+                t.flags = readc ? kFlagReadC : 0;
+                t.alpha = (float)g.alpha;
+                t.beta = (float)g.beta;
+                tasks.push_back(t);
+                const double bytes = 4.0 * ((double)mh * K + (double)K * nw + (double)mh * nw * (readc ? 2 : 1));
+                cost.push_back(ws_task_cost(vv, mh, nw, K, g.transA, g.transB, readc) + kWsByteSlots * bytes);
+            }
+        }
+    }
+
+    iaat_plan_s *plan = new (std::nothrow) iaat_plan_s;
+    if (!plan)
+        return fail(IAAT_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e != cudaSuccess) {
+        delete plan;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    iaat_status_t ps = prepare_device(plan->device, 8);
+    if (ps != IAAT_OK) {
+        delete plan;
+        return ps;
+    }
+    plan->ws = true;
+    plan->esz = 4;
+    plan->dtype = IAAT_F32;
+    plan->precision = IAAT_PREC_DEFAULT;
+    const int64_t nt = (int64_t)tasks.size();
+    const int sms = sm_count(plan->device);
+    const int grid = (int)std::min<int64_t>(nt, (int64_t)sms);
+    const int nwarps = grid * kWsWarps;
+
+    // Largest-cost-first assignment, each task to the least loaded warp;
+    // equal loads go to the warp that comes first in the order warp 0 of
+    // every CTA, then warp 1 of every CTA, ..., so small batches spread over
+    // the SMs before they share one.
+    std::vector<int32_t> wbeg((size_t)nwarps + 1, 0);
+    std::vector<WsTask> flat((size_t)nt);
+    if (nt > 0) {
+        std::vector<int32_t> order((size_t)nt);
+        for (int64_t k = 0; k < nt; ++k)
+            order[(size_t)k] = (int32_t)k;
+        std::stable_sort(order.begin(), order.end(), [&cost](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+        using Slot = std::pair<double, int32_t>;   // (load, rank of the warp)
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int r = 0; r < nwarps; ++r)
+            heap.push(Slot(0.0, r));
+        std::vector<int32_t> owner((size_t)nt);
+        std::vector<int32_t> per((size_t)nwarps, 0);
+        for (int32_t k : order) {
+            Slot s = heap.top();
+            heap.pop();
+            const int r = s.second;
+            const int w = (r % grid) * kWsWarps + r / grid;   // CTA r % grid, warp r / grid
+            owner[(size_t)k] = w;
+            ++per[(size_t)w];
+            s.first += cost[(size_t)k];
+            heap.push(s);
+        }
+        for (int w = 0; w < nwarps; ++w)
+            wbeg[(size_t)w + 1] = wbeg[(size_t)w] + per[(size_t)w];
+        std::vector<int32_t> fill(wbeg.begin(), wbeg.end() - 1);
+        for (int32_t k : order)
+            flat[(size_t)fill[(size_t)owner[(size_t)k]]++] = tasks[(size_t)k];
+        if (opts && opts->inject_fault == 1)
+            flat[0].variant = 0xff;   // a record the kernel must refuse
+    }
+    const size_t tb = (size_t)std::max<int64_t>(nt, 1) * sizeof(WsTask);
+    const size_t wb = (((size_t)nwarps + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+    if ((e = cudaMalloc(&plan->d_ws, tb + wb + 256)) != cudaSuccess) {
+        plan->d_ws = nullptr;
+        iaat_plan_destroy(plan);
+        return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
+    }
+    if ((nt > 0 && (e = cudaMemcpy(plan->d_ws, flat.data(), (size_t)nt * sizeof(WsTask), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess) ||
+        (e = cudaMemcpy(plan->d_ws + tb, wbeg.data(), ((size_t)nwarps + 1) * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(plan->d_ws + tb + wb, 0, sizeof(int32_t))) != cudaSuccess) {
+        iaat_plan_destroy(plan);
+        return cuda_fail(e, "upload the warp tasks");
+    }
+    plan->wsp.tasks = reinterpret_cast<const WsTask *>(plan->d_ws);
+    plan->wsp.wbeg = reinterpret_cast<const int32_t *>(plan->d_ws + tb);
+    plan->wsp.err = reinterpret_cast<int32_t *>(plan->d_ws + tb + wb);
+    plan->wsp.nwarps = nwarps;
+    plan->d_err = plan->wsp.err;
+    plan->ntasks = nt;
+    plan->ngroups = nt > 0 ? nwarps : 0;
+    plan->grid = grid;
+    info.tasks = nt;
+    info.groups = plan->ngroups;
+    info.blocks = nt;
+    info.plan_bytes = (int64_t)(tb + wb + 256);
+    info.grid = grid;
+    info.kernels = nt > 0 ? 1 : 0;
+    plan->info = info;
+    *out = plan;
+    return IAAT_OK;
+}
+
+// ----------------------------------------- pack-stream tensor-core planner
+// Tensor-core plans run the pack-stream kernel (tc2.cuh).  Every instance is
+// one task, or is cut into row / column pieces (each with the whole K) when
+// it exceeds one MMA tile (128 rows, kT2Cols columns of C) or its raw
+// operands would take more than half a group's staging ring.  Tasks are sorted by K (largest first) and
+// placed into packs of up to kT2MaxTasks consecutive tasks (t2_layout: their
+// rows fill at most the 128 rows of the tile, their columns at most kT2Cols,
+// their staging at most half the ring),
+// so that instances of similar K share one MMA pass.  Each pack becomes a
+// program (header, task records with the staging offsets, bulk copies), and
+// the packs are dealt to the warp groups, largest first, each to the least
+// loaded group.
+struct T2Task {
+    TaskDesc d;
+    TaskStages st;
+};
+
+// Rows and columns of the tasks [t0, t0 + n) of a pack.  Tasks of more than
+// 32 rows take rows one after another from the start of quarter `rot` (or of
+// quarter 0 when they would not fit there); tasks of up to 32 rows each go
+// into one 32-row quarter (the rows of one epilogue warp), the quarter whose
+// warp has the fewest accumulator columns to read so far, ties going to the
+// first quarter from `rot` on.  Rotating `rot` from pack to pack spreads the
+// epilogue work over the four SM sub-partitions (warp q of every group runs
+// on sub-partition q).  Columns are handed out quarter by quarter, each
+// task's rounded up to 16, so that the columns a warp reads are one
+// contiguous run.  Returns false when the tasks do not fit (rows, or more
+// than kT2Cols columns); *ncols: the MMA N.
+static bool t2_layout(const std::vector<T2Task> &tasks, int64_t t0, int64_t n, int rot, int *row0, int *col0,
+                      int *ncols)
+{
+    int big_rows = 0;
+    for (int64_t k = 0; k < n; ++k)
+        if (tasks[(size_t)(t0 + k)].d.M > 32)
+            big_rows += tasks[(size_t)(t0 + k)].d.M;
+    if (big_rows > kTcPackRows)
+        return false;
+    const int big_start = 32 * rot + big_rows <= kTcPackRows ? 32 * rot : 0;
+    int big_end = big_start;
+    for (int64_t k = 0; k < n; ++k)
+        if (tasks[(size_t)(t0 + k)].d.M > 32) {
+            row0[k] = big_end;
+            big_end += tasks[(size_t)(t0 + k)].d.M;
+        }
+    int fill[4], load[4] = {0, 0, 0, 0}, quarter[kT2MaxTasks];
+    for (int q = 0; q < 4; ++q) {
+        // free rows of quarter q: all of it, or what the large tasks leave
+        const int lo = 32 * q, hi = 32 * q + 32;
+        fill[q] = (big_end <= lo || big_start >= hi) ? lo : (big_end < hi && big_start <= lo ? big_end : hi);
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        const TaskDesc &d = tasks[(size_t)(t0 + k)].d;
+        const int w = std::max(16, (d.N + 15) & ~15);
+        if (d.M > 32) {
+            quarter[k] = row0[k] / 32;
+            for (int q = row0[k] / 32; q <= (row0[k] + d.M - 1) / 32; ++q)
+                load[q] += w;
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        const TaskDesc &d = tasks[(size_t)(t0 + k)].d;
+        if (d.M > 32)
+            continue;
+        int best = -1;
+        for (int u = 0; u < 4; ++u) {
+            const int q = (rot + u) & 3;
+            if (fill[q] + d.M <= 32 * q + 32 && (best < 0 || load[q] < load[best]))
+                best = q;
+        }
+        if (best < 0)
+            return false;
+        row0[k] = fill[best];
+        fill[best] += d.M;
+        load[best] += std::max(16, (d.N + 15) & ~15);
+        quarter[k] = best;
+    }
+    int col = 0;
+    for (int q = 0; q < 4; ++q)
+        for (int64_t k = 0; k < n; ++k)
+            if (quarter[k] == q) {
+                col0[k] = col;
+                col += std::max(16, (tasks[(size_t)(t0 + k)].d.N + 15) & ~15);
+            }
+    *ncols = std::max(16, col);
+    return col <= kT2Cols;
+}
+
+static iaat_status_t plan_create_tc2(const iaat_gemm_desc_t *descs, int64_t count, iaat_precision_t precision,
+                                     const iaat_plan_options_t *opts, iaat_plan_t *out, const int64_t *index_map)
+{
+    // A pack takes at most half a group's ring, so two are always in flight
+    // (a group gives a pack's staging back before it waits for the next, so
+    // an empty ring always takes the next pack).
+    const uint32_t ring = (uint32_t)tc2_ring_bytes((int)precision);
+    const uint32_t pack_cap = (ring / 2) & ~15u;
+    const uint32_t task_cap = pack_cap - (uint32_t)(sizeof(Tc2Hdr) + sizeof(Tc2Rec));
+    const int kstep = precision == IAAT_PREC_TF32 ? 8 : 16;
+    std::vector<T2Task> tasks;
+    tasks.reserve((size_t)count);
+    iaat_plan_info_t info{};
+    info.instances = count;
+    info.dtype = IAAT_F32;
+    info.precision = precision;
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        const int64_t gi = index_map ? index_map[i] : i;
+        iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+                                          g.alpha, 4);
+        if (st != IAAT_OK)
+            return st;
+        const int M = g.M, N = g.N;
+        if (M == 0 || N == 0)
+            continue;
+        const int Keff = (g.alpha == 0.0) ? 0 : g.K;
+        if (Keff == 0 && g.beta == 1.0)
+            continue;
+        int pm = 1, pn = 1;
+        if (!choose_split(g, 4, Keff, task_cap, kTcPackRows, kT2Cols, pm, pn))
+            return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage (M=%d N=%d K=%d)",
+                        (long long)gi, M, N, g.K);
+        info.active += 1;
+        info.flops += 2 * (int64_t)M * N * Keff;
+        info.algorithmic_bytes +=
+            ((int64_t)M * Keff + (int64_t)Keff * N + (int64_t)M * N + (g.beta != 0.0 ? (int64_t)M * N : 0)) * 4;
+        for (int a = 0; a < pm; ++a) {
+            int r0, h;
+            piece_range(M, pm, a, r0, h);
+            for (int b = 0; b < pn; ++b) {
+                int c0, w;
+                piece_range(N, pn, b, c0, w);
+                T2Task t;
+                t.d = make_piece(g, 4, Keff, r0, h, c0, w);
+                t.st = plan_task(t.d, 4);
+                tasks.push_back(t);
+            }
+        }
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const T2Task &x, const T2Task &y) { return x.d.K > y.d.K; });
+
+    // packs: [first task, end) ranges over the sorted tasks, each as many
+    // consecutive tasks as t2_layout places, at most kT2MaxTasks and pack_cap
+    // bytes of staging
+    std::vector<int64_t> pbeg;
+    {
+        int row0[kT2MaxTasks], col0[kT2MaxTasks], ncols = 0;
+        int64_t first = 0;
+        uint32_t bytes = (uint32_t)sizeof(Tc2Hdr);
+        pbeg.push_back(0);
+        for (size_t k = 0; k < tasks.size(); ++k) {
+            const uint32_t b = tasks[k].st.total() + (uint32_t)sizeof(Tc2Rec);
+            const int64_t n = (int64_t)k - first + 1;
+            if ((int64_t)k > first && (n > kT2MaxTasks || bytes + b > pack_cap ||
+                                       !t2_layout(tasks, first, n, (int)(pbeg.size() - 1) & 3, row0, col0, &ncols))) {
+                pbeg.push_back((int64_t)k);
+                first = (int64_t)k;
+                bytes = (uint32_t)sizeof(Tc2Hdr);
+            }
+            bytes += b;
+        }
+        if (tasks.empty())
+            pbeg.clear();
+        pbeg.push_back((int64_t)tasks.size());
+    }
+    const int64_t npacks = (int64_t)pbeg.size() - 1;
+
+    // pack programs
+    std::vector<char> prog;
+    std::vector<int64_t> poff((size_t)std::max<int64_t>(npacks, 1), 0);
+    std::vector<double> pcost((size_t)std::max<int64_t>(npacks, 0));
+    std::vector<CopyCmd> cmds;
+    for (int64_t p = 0; p < npacks; ++p) {
+        const int64_t t0 = pbeg[(size_t)p], nt = pbeg[(size_t)p + 1] - t0;
+        Tc2Hdr h{};
+        h.ntasks = (int32_t)nt;
+        std::vector<Tc2Rec> recs((size_t)nt);
+        cmds.clear();
+        uint32_t off = (uint32_t)(sizeof(Tc2Hdr) + nt * sizeof(Tc2Rec));
+        h.rec_bytes = off;
+        uint32_t tx = off;
+        int row0[kT2MaxTasks], col0[kT2MaxTasks], ncols = 0, kmax = 0;
+        if (!t2_layout(tasks, t0, nt, (int)(p & 3), row0, col0, &ncols))
+            return fail(IAAT_ERR_INVALID_VALUE, "pack %lld: its tasks do not fit the tile", (long long)p);
+        double conv = 0.0;
+        for (int64_t k = 0; k < nt; ++k) {
+            const TaskDesc &d = tasks[(size_t)(t0 + k)].d;
+            const TaskStages &s = tasks[(size_t)(t0 + k)].st;
+            Tc2Rec &r = recs[(size_t)k];
+            r.C = d.C;
+            r.ldc = d.ldc;
+            r.offA = (int32_t)(off + ((uint32_t)(uintptr_t)d.A & 15u));
+            r.offB = (int32_t)(off + s.a.bytes + ((uint32_t)(uintptr_t)d.B & 15u));
+            r.offC = (int32_t)(off + s.a.bytes + s.b.bytes + ((uint32_t)(uintptr_t)d.C & 15u));
+            r.csA = (int32_t)s.a.cs;
+            r.csB = (int32_t)s.b.cs;
+            r.csC = (int32_t)s.c.cs;
+            r.K = d.K;
+            r.M = d.M;
+            r.N = d.N;
+            r.ta = d.ta;
+            r.tb = d.tb;
+            r.row0 = (uint8_t)row0[k];
+            r.col0 = (uint8_t)col0[k];
+            r.flags = d.flags;
+            r.alpha = (float)d.alpha;
+            r.beta = (float)d.beta;
+            kmax = std::max(kmax, (int)d.K);
+            int ha, wa, hb, wb;
+            stored_dims(d, ha, wa, hb, wb);
+            const bool prod = d.K > 0;
+            emit_copies(s.a, d.A, prod ? ha : 0, prod ? wa : 0, d.lda, 4, off, 0, cmds);
+            emit_copies(s.b, d.B, prod ? hb : 0, prod ? wb : 0, d.ldb, 4, off + s.a.bytes, 0, cmds);
+            emit_copies(s.c, d.C, d.M, d.N, d.ldc, 4, off + s.a.bytes + s.b.bytes, 0, cmds);
+            tx += s.a.tx + s.b.tx + s.c.tx;
+            off += s.total();
+            conv += (double)(d.M + d.N) * ((d.K + kT2KC - 1) / kT2KC);
+        }
+        h.ncmd = (int32_t)cmds.size();
+        h.kpack = kmax > 0 ? (kmax + kstep - 1) / kstep * kstep : 0;
+        h.nt = ncols;
+        h.item_bytes = off;
+        h.tx_bytes = tx;
+        if (off > pack_cap || off > ring)
+            return fail(IAAT_ERR_UNSUPPORTED, "pack %lld needs %u bytes of staging", (long long)p, off);
+        // every access the kernel derives from the program stays inside the
+        // pack's staging item, its tile and its operand buffers
+        {
+            uint64_t sum = h.rec_bytes;
+            for (const CopyCmd &c : cmds) {
+                const uint32_t b = c.meta & 0xffffffu;
+                if (c.dst < h.rec_bytes || c.dst + b > off || ((c.dst | b | (uint32_t)(uintptr_t)c.src) & 15u))
+                    return fail(IAAT_ERR_INVALID_VALUE, "pack %lld: copy outside its staging item", (long long)p);
+                sum += b;
+            }
+            if (sum != tx || h.nt > kT2Cols || (h.nt & 15))
+                return fail(IAAT_ERR_INVALID_VALUE, "pack %lld: inconsistent program", (long long)p);
+            auto inside = [&](int32_t o, int32_t cs, int rows, int cols) {
+                if (rows <= 0 || cols <= 0)
+                    return true;
+                const int64_t last = (int64_t)o + (int64_t)(cols - 1) * cs + (int64_t)rows * 4;
+                return o >= (int32_t)h.rec_bytes && last <= (int64_t)off;
+            };
+            for (int64_t k = 0; k < nt; ++k) {
+                const Tc2Rec &r = recs[(size_t)k];
+                const int K = r.K, M = r.M, N = r.N;
+                const bool okA = inside(r.offA, r.csA, r.ta ? K : M, r.ta ? M : K);
+                const bool okB = inside(r.offB, r.csB, r.tb ? N : K, r.tb ? K : N);
+                const bool okC = !(r.flags & kFlagReadC) || inside(r.offC, r.csC, M, N);
+                bool overlap = false;   // rows and column runs of the pack's tasks are disjoint
+                for (int64_t k2 = 0; k2 < k; ++k2) {
+                    const Tc2Rec &o = recs[(size_t)k2];
+                    overlap = overlap || (r.row0 < o.row0 + o.M && o.row0 < r.row0 + M) ||
+                              (r.col0 < o.col0 + ((o.N + 15) & ~15) && o.col0 < r.col0 + ((N + 15) & ~15));
+                }
+                if (!okA || !okB || !okC || overlap || r.row0 + M > 128 || r.col0 + ((N + 15) & ~15) > h.nt)
+                    return fail(IAAT_ERR_INVALID_VALUE, "pack %lld: task %lld outside its staging or tile",
+                                (long long)p, (long long)k);
+            }
+        }
+        poff[(size_t)p] = (int64_t)prog.size();
+        auto put = [&prog](const void *x, size_t n) {
+            const char *c = static_cast<const char *>(x);
+            prog.insert(prog.end(), c, c + n);
+        };
+        put(&h, sizeof h);
+        put(recs.data(), recs.size() * sizeof(Tc2Rec));
+        prog.resize(prog.size() + (kT2MaxTasks - recs.size()) * sizeof(Tc2Rec), 0);   // commands at kT2CmdOff
+        put(cmds.data(), cmds.size() * sizeof(CopyCmd));
+        // one pack: its bytes at the HBM rate plus its conversion and epilogue work
+        pcost[(size_t)p] = (double)tx + 64.0 * conv + 2048.0;
+    }
+    // the issuing warp prefetches a fixed window of kT2Window bytes of each
+    // program before it knows the program's size: pad the programs so that
+    // the window of the last one stays inside them
+    prog.resize(prog.size() + kT2Window, 0);
+    if (opts && opts->inject_fault == 1 && npacks > 0)
+        reinterpret_cast<Tc2Hdr *>(prog.data() + poff[0])->ntasks = kT2MaxTasks + 1;
+
+    iaat_plan_s *plan = new (std::nothrow) iaat_plan_s;
+    if (!plan)
+        return fail(IAAT_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e != cudaSuccess) {
+        delete plan;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    iaat_status_t ps = prepare_device(plan->device, 8 + (int)precision);
+    if (ps != IAAT_OK) {
+        delete plan;
+        return ps;
+    }
+    plan->tc2 = true;
+    plan->esz = 4;
+    plan->dtype = IAAT_F32;
+    plan->precision = precision;
+    const int sms = sm_count(plan->device);
+    const int grid = (int)std::min<int64_t>((npacks + kT2Groups - 1) / kT2Groups, (int64_t)sms);
+    const int ngr = grid * kT2Groups;
+
+    // deal the packs to the groups: largest first, each to the least loaded
+    // group; equal loads go to group 0 of every CTA first, then group 1, ...
+    std::vector<int32_t> gbeg((size_t)ngr + 1, 0);
+    std::vector<int64_t> poff_sorted((size_t)std::max<int64_t>(npacks, 1), 0);
+    if (npacks > 0) {
+        std::vector<int32_t> order((size_t)npacks);
+        for (int64_t k = 0; k < npacks; ++k)
+            order[(size_t)k] = (int32_t)k;
+        std::stable_sort(order.begin(), order.end(), [&pcost](int32_t a, int32_t b) { return pcost[a] > pcost[b]; });
+        using Slot = std::pair<double, int32_t>;
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int r = 0; r < ngr; ++r)
+            heap.push(Slot(0.0, r));
+        std::vector<int32_t> owner((size_t)npacks), per((size_t)ngr, 0);
+        for (int32_t k : order) {
+            Slot sl = heap.top();
+            heap.pop();
+            const int r = sl.second;
+            const int gid = (r % grid) * kT2Groups + r / grid;
+            owner[(size_t)k] = gid;
+            ++per[(size_t)gid];
+            sl.first += pcost[(size_t)k];
+            heap.push(sl);
+        }
+        for (int gid = 0; gid < ngr; ++gid)
+            gbeg[(size_t)gid + 1] = gbeg[(size_t)gid] + per[(size_t)gid];
+        std::vector<int32_t> fill(gbeg.begin(), gbeg.end() - 1);
+        for (int32_t k : order)
+            poff_sorted[(size_t)fill[(size_t)owner[(size_t)k]]++] = poff[(size_t)k];
+        // every header names the programs of the next two packs of its group,
+        // so the issuing warp never waits for a global load
+        for (int gid = 0; gid < ngr; ++gid)
+            for (int32_t k = gbeg[(size_t)gid]; k < gbeg[(size_t)gid + 1]; ++k) {
+                Tc2Hdr *h = reinterpret_cast<Tc2Hdr *>(prog.data() + poff_sorted[(size_t)k]);
+                h->next[0] = k + 1 < gbeg[(size_t)gid + 1] ? poff_sorted[(size_t)k + 1] : -1;
+                h->next[1] = k + 2 < gbeg[(size_t)gid + 1] ? poff_sorted[(size_t)k + 2] : -1;
+            }
+    }
+    const size_t pb = std::max<size_t>(16, prog.size());
+    const size_t ob = poff_sorted.size() * sizeof(int64_t), gb = gbeg.size() * sizeof(int32_t);
+    if ((e = cudaMalloc(&plan->d_prog, pb)) != cudaSuccess || (e = cudaMalloc(&plan->d_poff, ob)) != cudaSuccess ||
+        (e = cudaMalloc(&plan->d_gbeg, gb)) != cudaSuccess || (e = cudaMalloc(&plan->d_err, sizeof(int32_t))) != cudaSuccess) {
+        iaat_plan_destroy(plan);
+        return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
+    }
+    if ((!prog.empty() && (e = cudaMemcpy(plan->d_prog, prog.data(), prog.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(plan->d_poff, poff_sorted.data(), ob, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(plan->d_gbeg, gbeg.data(), gb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(plan->d_err, 0, sizeof(int32_t))) != cudaSuccess) {
+        iaat_plan_destroy(plan);
+        return cuda_fail(e, "upload the pack programs");
+    }
+    plan->t2p.prog = plan->d_prog;
+    plan->t2p.poff = plan->d_poff;
+    plan->t2p.gbeg = plan->d_gbeg;
+    plan->t2p.err = plan->d_err;
+    plan->t2p.ngroups = ngr;
+    plan->ntasks = (int64_t)tasks.size();
+    plan->ngroups = npacks > 0 ? ngr : 0;
+    plan->grid = grid;
+    info.tasks = plan->ntasks;
+    info.groups = npacks;
+    info.blocks = npacks;
+    info.plan_bytes = (int64_t)(pb + ob + gb + sizeof(int32_t));
+    info.grid = grid;
+    info.kernels = npacks > 0 ? 1 : 0;
+    plan->info = info;
+    *out = plan;
+    return IAAT_OK;
+}
+
 // The planner behind iaat_plan_create and iaat_plan_create_complex.  cscal:
 // complex plans only, (re alpha, im alpha, re beta, im beta) per instance,
 // already rounded to the component type; the descriptors then carry alpha
@@ -735,6 +1340,13 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
             ctas_per_sm = 1;   // the kernel takes all shared memory: one CTA per SM
     }
     (void)ctas_per_sm;
+    const int kernel = opts ? opts->kernel : 0;
+    if (kernel < 0 || kernel > 2)
+        return fail(IAAT_ERR_INVALID_VALUE, "kernel %d out of range", kernel);
+    if (dt == IAAT_F32 && !tc && kernel == 2)
+        return plan_create_ws(descs, count, opts, force_variant, out, index_map);
+    if (tc && kernel == 2)
+        return plan_create_tc2(descs, count, precision, opts, out, index_map);
 
     std::vector<HostTask> tasks;
     tasks.reserve((size_t)count);
@@ -965,6 +1577,16 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
         return fail(IAAT_ERR_INVALID_VALUE, "plan is NULL");
     if (plan->ngroups == 0)
         return plan->sub ? iaat_gemm_grouped(plan->sub, stream) : IAAT_OK;
+    if (plan->ws || plan->tc2) {
+        const cudaError_t e = plan->ws ? launch_ws(plan->wsp, plan->grid, static_cast<cudaStream_t>(stream))
+                                       : launch_tc2((int)plan->precision, plan->t2p, plan->grid,
+                                                    static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel launch");
+        if (plan->sub)   // routed small-K instances, after the tensor-core launch on the same stream
+            return iaat_gemm_grouped(plan->sub, stream);
+        return IAAT_OK;
+    }
     KParams kp;
     std::memset(&kp, 0, sizeof kp);
     kp.p.prog = plan->d_prog;
@@ -1048,8 +1670,12 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
         cudaFree(plan->d_prog);
     if (plan->d_poff)
         cudaFree(plan->d_poff);
-    if (plan->d_err)
+    if (plan->d_err && !plan->ws)
         cudaFree(plan->d_err);
+    if (plan->d_ws)
+        cudaFree(plan->d_ws);
+    if (plan->d_gbeg)
+        cudaFree(plan->d_gbeg);
     if (plan->d_scal)
         cudaFree(plan->d_scal);
     if (cur >= 0 && cur != plan->device)

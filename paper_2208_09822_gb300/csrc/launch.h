@@ -6,6 +6,9 @@
 
 namespace iaat {
 cudaError_t prepare_fma(int dtype);
+// warp-stream FP32 kernel (ws.cuh)
+cudaError_t prepare_ws();
+cudaError_t launch_ws(const WsParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_fma(int dtype, const KParams &kp, int grid, cudaStream_t stream);
 cudaError_t single_call_err_ptr(int32_t **p);
 cudaError_t measure_fma_peak(int dtype, double *gflops);   // 0 FP32 FFMA, 1 FP64 DFMA
@@ -13,6 +16,10 @@ cudaError_t measure_fma_peak(int dtype, double *gflops);   // 0 FP32 FFMA, 1 FP6
 cudaError_t prepare_tc(int precision);
 cudaError_t launch_tc(int precision, const KParams &kp, int grid, cudaStream_t stream);
 int tc_group_cap(int precision);        // largest stage footprint (bytes)
+// pack-stream tensor-core kernel (tc2.cuh)
+cudaError_t prepare_tc2(int precision);
+cudaError_t launch_tc2(int precision, const Tc2Params &p, int grid, cudaStream_t stream);
+int tc2_ring_bytes(int precision);      // staging ring of one warp group (bytes)
 // complex kernel (CGEMM / ZGEMM), dtype IAAT_C32 or IAAT_C64
 cudaError_t prepare_cplx(int dtype);
 cudaError_t launch_cplx(int dtype, const KParams &kp, int grid, cudaStream_t stream);

@@ -354,6 +354,7 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
         std::fprintf(f, "  \"variant_scale_f32\": [");
         for (int v = 0; v < kNumVariantsF32; ++v)
             std::fprintf(f, "%s%.4f", v ? ", " : "", t.scale_f32[v]);
+
         std::fprintf(f, "],\n  \"variant_scale_f64\": [");
         for (int v = 0; v < kNumVariantsF64; ++v)
             std::fprintf(f, "%s%.4f", v ? ", " : "", t.scale_f64[v]);

@@ -71,16 +71,17 @@ def test_domain_boundary_is_inclusive(L):
     assert W.in_domain(32, 32, 33, 1, 1)   # TT keeps the larger bound
 
 
-@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("K", [20000, 40000])
-def test_plan_create_rejects_unstageable_k(L, prec, K):
+def test_plan_create_rejects_unstageable_k(L, K):
     """1 x 1 x K is small (MNK <= 512000) but a row of A and a column of B
-    that long do not fit one pipeline stage, and K is never cut: rejected
-    with UNSUPPORTED, before any device work."""
-    with pytest.raises(iaat.IaatError) as e:
-        iaat.iaat_plan_create(_desc(M=1, N=1, K=K, lda=1, ldb=K, ldc=1), iaat.IAAT_F32, prec)
-    assert e.value.status == 4
-    assert "instance 0" in e.value.message
+    that long do not fit one pipeline stage of the tensor-core kernel or of
+    the stage-program CUDA-core kernel, and those never cut K: rejected with
+    UNSUPPORTED, before any device work."""
+    for prec, kernel in ((1, 0), (0, 1)):
+        with pytest.raises(iaat.IaatError) as e:
+            iaat.iaat_plan_create(_desc(M=1, N=1, K=K, lda=1, ldb=K, ldc=1), iaat.IAAT_F32, prec, kernel=kernel)
+        assert e.value.status == 4
+        assert "instance 0" in e.value.message
 
 
 @pytest.mark.parametrize("prec", [iaat.IAAT_PREC_3XBF16, iaat.IAAT_PREC_6XBF16])
