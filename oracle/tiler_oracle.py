@@ -5,20 +5,26 @@ import this module.  It shares nothing with the library.
 
 Contents
 --------
-* ``tile_single_dim``  -- the one-dimension splitter used by Algorithm 2
-  (Sec. V-A, "TileSingleDim"): greedy runs of the largest size, and a last
-  piece that is "too small" averaged with the one before it.
-* ``sgemm_nn_tile``    -- Algorithm 2 (Sec. V-A), the SGEMM_NN tiler, taken
-  case by case in the paper's order and notation.
+* ``tile_single_dim``  -- the one-dimension splitter of Sec. V-A
+  ("TileSingleDim"): as many pieces of the largest usable size as fit, and a
+  last piece that is "too small" averaged with the one before it.
+* ``sgemm_nn_tile``    -- the SGEMM_NN tiling of C (Sec. V-A, Algorithm 2),
+  written from the section's rules: narrow C (N <= 13) is one column of
+  width N cut into the tallest rows that width allows; wide C is cut into
+  row strips built from 4-row strips with 1-, 2- and 3-row strips for the
+  remainder (merged into 8- or 16-row strips when M > 12, whichever moves
+  fewer values), and every strip is cut across N into the widest blocks
+  its height allows.
+* ``blocks_ab``        -- the blocks of A and B the C blocks read.
 * ``memops``           -- the "Minimal Memops" count of Sec. V-A:
   (m_0+n_0+...+m_a+n_a)*K + 2*M*N values moved between cache and registers.
 * ``min_strip_memops`` -- exhaustive search over every row-strip tiling (each
   strip split into blocks) for the smallest sum(m_i+n_i), tiny sizes only.
 
 Readings where the paper is silent or garbled (the builder's choices):
-1. A remainder that is not itself a kernel height (Algorithm 2, N <= 13 branch)
-   is tiled again with the same rule: the largest height whose kernel row
-   holds width N, repeated while it fits.
+1. A remainder of a narrow C that is not itself a kernel height is tiled
+   again with the same rule: the tallest height whose kernels reach width N,
+   repeated while it fits.
 2. TileSingleDim's "too small" is "less than half of the largest piece"; the
    last full piece and the remainder are then replaced by the two halves of
    their sum (ceil, floor).  This leaves sum(n) and the piece count unchanged.
@@ -26,17 +32,19 @@ Readings where the paper is silent or garbled (the builder's choices):
    groups of four into 16-row strips, and a leftover of three, two or one
    4-row strips becomes one 12-, 8- or 4-row strip.  The 15x15 example needs
    three 4-row strips to become one 12-row strip.
-4. CompareLessMemops keeps the first candidate on a tie.
+4. Of the two merges, the first (8-row strips) is kept on a tie.
 5. "2mn" in the memops formula is 2*M*N (one load and one store of C); the
    worked example's 450 = 2*15*15 fixes this.
+6. Every strip is cut across N with the widths its height's kernels reach
+   (the outline's "maximum value that n_c can be taken"); where the printed
+   steps give a 3-row strip widths up to 8 (M = 4q + 1 > 12), the oracle
+   follows the outline and gives it the 13 its kernels reach.
 
 Shape sets are passed in as {height: max_width}: a kernel m_c x n_c exists for
 every width 1..max_width of that height (that is how every row of Table I is
 written).
 """
 from __future__ import annotations
-
-from itertools import product as _product
 
 
 def tile_single_dim(length, sizes):
@@ -66,23 +74,18 @@ def tile_single_dim(length, sizes):
     return [(d, c) for d, c in runs if c > 0]
 
 
-def _widths(maxw):
-    return list(range(1, maxw + 1))
-
-
-def _combine(mruns, nlists):
-    """Combine(m, n): strip runs m[r] = (height, count), each strip split by
-    the column runs nlists[r]; return blocks (row0, col0, m_c, n_c)."""
+def _strip_blocks(heights, N, shapes):
+    """Blocks (row0, col0, m_c, n_c) of row strips of the given heights (top
+    to bottom), each cut across N into the widest blocks its height allows."""
     blocks = []
     row = 0
-    for (h, cnt), nruns in zip(mruns, nlists):
-        for _ in range(cnt):
-            col = 0
-            for w, wc in nruns:
-                for _ in range(wc):
-                    blocks.append((row, col, h, w))
-                    col += w
-            row += h
+    for h in heights:
+        col = 0
+        for w, count in tile_single_dim(N, range(1, shapes[h] + 1)):
+            for _ in range(count):
+                blocks.append((row, col, h, w))
+                col += w
+        row += h
     return blocks
 
 
@@ -90,87 +93,78 @@ def _strip_sum(blocks):
     return sum(m + n for _, _, m, n in blocks)
 
 
-def _extend(q, group):
-    """ExtendTo8 (group=2) / ExtendTo16 (group=4) on q strips of height 4."""
-    runs = []
+def _merge_fours(q, group):
+    """q 4-row strips merged into strips of 4*group rows, a leftover of
+    fewer than `group` of them into one strip (reading 3)."""
     full, left = divmod(q, group)
-    if full:
-        runs.append((4 * group, full))
-    if left:
-        runs.append((4 * left, 1))
-    return runs
+    return [4 * group] * full + ([4 * left] if left else [])
+
+
+def _narrow_heights(M, N, shapes):
+    """Row strips of a narrow C: the tallest height whose kernels reach
+    width N, as often as it fits, then the remainder the same way."""
+    heights = []
+    rem = M
+    while rem:
+        h = max(x for x in shapes if x <= rem and shapes[x] >= N)
+        heights += [h] * (rem // h)
+        rem %= h
+    return heights
+
+
+def _wide_heights(M):
+    """Candidate row strips of a wide C (N > 13), each a list of heights.
+
+    4-row strips, with 1-, 2- and 3-row strips making up M; the kernel set
+    of Table I fixes the small cases: up to 7 rows the strips TileSingleDim
+    cuts from heights 1..4, 9 rows as 4 + 3 + 2, 10 and 11 rows as an 8-row
+    strip and the rest, 12 rows as one strip.  Beyond 12 rows the 4-row
+    strips are merged into 8- or 16-row strips (two candidates); a remainder
+    of one row is avoided by giving up one 4-row strip for 3 + 2."""
+    if M < 8:
+        return [[h for h, c in tile_single_dim(M, [1, 2, 3, 4]) for _ in range(c)]]
+    if M == 8:
+        return [[8]]
+    if M == 9:
+        return [[4, 3, 2]]
+    if M < 12:
+        return [[8, M - 8]]
+    if M == 12:
+        return [[12]]
+    q, r = divmod(M, 4)
+    tail = [r] if r else []
+    if r == 1:
+        q, tail = q - 1, [3, 2]
+    return [_merge_fours(q, 2) + tail, _merge_fours(q, 4) + tail]
 
 
 def sgemm_nn_tile(M, N, shapes):
-    """Algorithm 2 (Sec. V-A): SGEMM_NN tile algorithm.
+    """The SGEMM_NN tiling of C (Sec. V-A, Algorithm 2).
 
     ``shapes`` is the SGEMM_NN row of Table I as {height: max_width}.
-    Returns blocksC as a list of (row0, col0, m_c, n_c); blocksA / blocksB
-    follow from it (rows row0.. of A with all K columns, columns col0.. of B
-    with all K rows) and are returned by ``blocks_ab``.
+    Returns blocksC as a list of (row0, col0, m_c, n_c); ``blocks_ab`` gives
+    the blocks of A and B they read.
     """
     if M <= 0 or N <= 0:
         return []
-    heights = sorted(shapes, reverse=True)
     if N <= 13:
-        # m_1: largest kernel height whose row holds width N; I = floor(M/m_1)
-        def tallest(limit):
-            return max(h for h in heights if h <= limit and shapes[h] >= N)
-        m1 = tallest(max(heights))
-        I = M // m1
-        mruns = [(m1, I)] if I else []
-        rem = M - m1 * I
-        while rem:  # reading 1: the remainder tiled with the same rule
-            h = tallest(rem)
-            c = rem // h
-            mruns.append((h, c))
-            rem -= h * c
-        nlists = [[(N, 1)] for _ in mruns]
-        return _combine(mruns, nlists)
-    w13, w8, w6 = _widths(13), _widths(8), _widths(6)
-    if M < 8:
-        mruns = tile_single_dim(M, [1, 2, 3, 4])
-        nlists = [tile_single_dim(N, w13)]
-        if len(mruns) == 2:
-            nlists.append(tile_single_dim(N, w13))
-        return _combine(mruns, nlists)
-    if M == 9:
-        mruns = [(4, 1), (3, 1), (2, 1)]
-        nlists = [tile_single_dim(N, w13) for _ in range(3)]
-        return _combine(mruns, nlists)
-    if M < 12:
-        mruns = [(8, 1)]
-        nlists = [tile_single_dim(N, w8)]
-        if M - 8:
-            mruns.append((M - 8, 1))
-            nlists.append(tile_single_dim(N, w13))
-        return _combine(mruns, nlists)
-    if M == 12:
-        return _combine([(12, 1)], [tile_single_dim(N, w6)])
-    # M > 12
-    q = M // 4
-    r = M - 4 * q
-    m2 = [(r, 1)] if r else []
-    n2 = [tile_single_dim(N, w13)] if r else []
-    if r == 1:
-        q -= 1
-        m2 = [(3, 1), (2, 1)]
-        n2 = [tile_single_dim(N, w8), tile_single_dim(N, w13)]
-    m8 = _extend(q, 2)
-    m16 = _extend(q, 4)
-    n8 = [tile_single_dim(N, _widths(shapes[h])) for h, _ in m8]
-    n16 = [tile_single_dim(N, _widths(shapes[h])) for h, _ in m16]
-    c1 = _combine(m8, n8)
-    c2 = _combine(m16, n16)
-    best = c2 if _strip_sum(c2) < _strip_sum(c1) else c1  # reading 4
-    top = 4 * q
-    tail = [(row + top, col, m, n) for row, col, m, n in _combine(m2, n2)]
-    return best + tail
+        heights = _narrow_heights(M, N, shapes)
+        blocks, row = [], 0
+        for h in heights:
+            blocks.append((row, 0, h, N))
+            row += h
+        return blocks
+    best = None
+    for heights in _wide_heights(M):   # the fewer values moved wins; the first on a tie
+        blocks = _strip_blocks(heights, N, shapes)
+        if best is None or _strip_sum(blocks) < _strip_sum(best):
+            best = blocks
+    return best
 
 
 def blocks_ab(blocksC, K):
-    """blocksA / blocksB of Algorithm 2: the A rows and B columns each C
-    block reads, as (row0, m_c, K) and (col0, n_c, K)."""
+    """blocksA / blocksB of Sec. V-A: the A rows and B columns each C block
+    reads, as (row0, m_c, K) and (col0, n_c, K), in the order of blocksC."""
     return ([(r, m, K) for r, _, m, _ in blocksC],
             [(c, n, K) for _, c, _, n in blocksC])
 

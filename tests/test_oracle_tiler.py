@@ -105,3 +105,37 @@ def test_memops_counts_loads():
             loads += n   # one row of the B block
     loads += 2 * M * N
     assert T.memops(blocks, M, N, K) == loads
+
+
+def test_blocks_ab_compute_the_product(nn_shapes):
+    """blocksA / blocksB are the slices of A and B each C block reads: a
+    blocked product that takes, for every C block, the A rows and B columns
+    blocks_ab names equals A @ B, and their element count is the memops
+    count of the tiling minus the 2*M*N values of C."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    for M, N, K in ((15, 15, 7), (9, 20, 3), (40, 3, 5), (29, 31, 4), (13, 14, 2)):
+        A = rng.integers(-4, 5, (M, K))
+        B = rng.integers(-4, 5, (K, N))
+        blocks = T.sgemm_nn_tile(M, N, nn_shapes)
+        ba, bb = T.blocks_ab(blocks, K)
+        assert len(ba) == len(bb) == len(blocks)
+        C = np.zeros((M, N), np.int64)
+        for (r, c, m, n), (ra, ma, ka), (cb, nb, kb) in zip(blocks, ba, bb):
+            assert (ra, ma, ka) == (r, m, K) and (cb, nb, kb) == (c, n, K)
+            C[r:r + m, c:c + n] += A[ra:ra + ma, :ka] @ B[:kb, cb:cb + nb]
+        assert np.array_equal(C, A @ B)
+        loads = sum(m * k for _, m, k in ba) + sum(n * k for _, n, k in bb)
+        assert loads + 2 * M * N == T.memops(blocks, M, N, K)
+
+
+def test_remainder_of_one_row(nn_shapes):
+    """M = 4q + 1 beyond 12 rows: one 4-row strip gives way to a 3- and a
+    2-row strip, each cut across N with the widths its height's kernels
+    reach (reading 6: 13 for both)."""
+    for M in (13, 17, 41, 77):
+        b = T.sgemm_nn_tile(M, 40, nn_shapes)
+        hs = sorted({(r, m) for r, _, m, _ in b})
+        assert [m for _, m in hs][-2:] == [3, 2], (M, hs)
+        assert max(n for _, _, m, n in b if m == 3) == 13
+        assert all(m != 1 for _, _, m, _ in b)
