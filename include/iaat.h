@@ -162,10 +162,13 @@ typedef struct {
 
 /* Single small GEMM, FP32 / FP64 (BLAS sgemm/dgemm argument order, Sec. I).
  * Device pointers; asynchronous on `stream`.  The instance's tasks travel in
- * the kernel's parameter block, so the call allocates nothing; a device-side
- * time-out is reported by iaat_plan_check(NULL, stream).  For the paper's
- * "same size repeatedly" use (Sec. VII), a plan (iaat_plan_create) keeps the
- * tiling and descriptors on the device and replays them. */
+ * the kernel's parameter block, at most 32 per launch, so the call allocates
+ * nothing and shares no device state with other calls (an instance cut into
+ * more pieces, such as 512000 x 1 x 1, takes several launches in a row on
+ * `stream`); a device-side time-out is reported by iaat_plan_check(NULL,
+ * stream).  For the paper's "same size repeatedly" use (Sec. VII), a plan
+ * (iaat_plan_create) keeps the tiling and descriptors on the device and
+ * replays them. */
 iaat_status_t iaat_sgemm(int transA, int transB, int M, int N, int K,
                          float alpha, const float *A, int lda,
                          const float *B, int ldb, float beta, float *C,
@@ -213,11 +216,13 @@ iaat_status_t iaat_zgemm(int transA, int transB, int M, int N, int K,
  * column pieces when its operands do not fit one pipeline stage); larger
  * batches return IAAT_ERR_INVALID_VALUE and enqueue nothing.
  * The first call on a device looks up the scratch array's device address
- * (and reads the tuning cache); make that first call before any stream
- * capture.  Every call reuses the same scratch array and the kernel reads it
- * while it runs, so calls that overlap on the GPU (other streams, other
- * threads) race and give wrong results: order them on one stream.  A device
- * time-out is reported by iaat_plan_check(NULL, stream). */
+ * (and reads the tuning cache).  The call cannot be captured in a CUDA
+ * graph: it copies each call's plan from host arrays that the next call
+ * reuses, so on a capturing stream it returns IAAT_ERR_UNSUPPORTED and
+ * enqueues nothing.  Every call reuses the same scratch array and the kernel
+ * reads it while it runs, so calls that overlap on the GPU (other streams,
+ * other threads) race and give wrong results: order them on one stream.  A
+ * device time-out is reported by iaat_plan_check(NULL, stream). */
 iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t count,
                                         iaat_dtype_t dtype, void *stream);
 
@@ -253,18 +258,29 @@ iaat_status_t iaat_plan_create_complex(const iaat_cgemm_desc_t *descs, int64_t c
 iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream);
 
 /* Synchronise `stream`, then report (and clear) a device-side error of the
- * plan's kernels: IAAT_ERR_DEVICE_TIMEOUT if a bounded wait gave up. */
+ * plan's kernels: IAAT_ERR_DEVICE_TIMEOUT if a bounded wait gave up or a
+ * malformed plan record was refused.  plan == NULL checks the error words of
+ * the single calls and of the allocation-free entry point; both are read and
+ * cleared, and the first error is returned.  Sec. V-B runs a plan's kernels;
+ * this is the host's view of how that run ended. */
 iaat_status_t iaat_plan_check(iaat_plan_t plan, void *stream);
 
 iaat_status_t iaat_plan_info(iaat_plan_t plan, iaat_plan_info_t *info);
 
-/* Free the plan's device memory (synchronises the device first). */
+/* Free the plan's device memory (synchronises the device first).  The
+ * counterpart of building the kernel executing plan (Sec. V-B): a plan can
+ * be replayed any number of times until it is destroyed. */
 iaat_status_t iaat_plan_destroy(iaat_plan_t plan);
 
-/* Time the register-tile variants on the current GPU for (dtype, precision)
- * and write the per-shape-class winners as JSON to `cache_path` (NULL: the
- * path in IAAT_TUNE_CACHE, else no file).  Later plans read the cache named
- * by IAAT_TUNE_CACHE.  Synchronous; allocates its own test matrices. */
+/* Install-time tuning (Sec. III-A and Sec. IV: the kernels are tuned once
+ * for the hardware they run on).  Times the register-tile variants on the
+ * current GPU for (dtype, precision) and the stage size on an uneven batch,
+ * and writes the per-variant cost scales and stage sizes as JSON to
+ * `cache_path` (NULL: the path in IAAT_TUNE_CACHE, else no file), together
+ * with the GPU's name, SM count, driver and runtime versions.  Later
+ * processes read the cache named by IAAT_TUNE_CACHE and ignore it when any
+ * of those differ from the current GPU's.  Synchronous; allocates its own
+ * test matrices. */
 iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t precision,
                             const char *cache_path);
 
@@ -318,7 +334,10 @@ int64_t iaat_tile_exact(int M, int N, const int32_t *heights,
 /* Version string of the library. */
 const char *iaat_version(void);
 
-/* Message for the calling thread's last failing call ("" if none). */
+/* Message for the calling thread's last failing call ("" if none): which
+ * instance broke which rule of Sec. I's domain or of the BLAS argument
+ * rules, or which CUDA call failed.  Thread-local; valid until the thread's
+ * next failing call. */
 const char *iaat_last_error(void);
 
 #ifdef __cplusplus

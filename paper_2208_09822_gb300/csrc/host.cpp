@@ -1639,12 +1639,10 @@ extern "C" iaat_status_t iaat_plan_check(iaat_plan_t plan, void *stream)
     int32_t *w2 = nullptr;
     if ((e = noalloc_err_ptr(&w2)) != cudaSuccess)
         return cuda_fail(e, "cudaGetDevice");
-    if (w2) {
-        const iaat_status_t st = read_and_clear(w2, static_cast<cudaStream_t>(stream));
-        if (st != IAAT_OK)
-            return st;
-    }
-    return read_and_clear(w, static_cast<cudaStream_t>(stream));
+    // both words are read and cleared; the first error found is returned
+    const iaat_status_t st1 = w2 ? read_and_clear(w2, static_cast<cudaStream_t>(stream)) : IAAT_OK;
+    const iaat_status_t st2 = read_and_clear(w, static_cast<cudaStream_t>(stream));
+    return st1 != IAAT_OK ? st1 : st2;
 }
 
 extern "C" iaat_status_t iaat_plan_info(iaat_plan_t plan, iaat_plan_info_t *info)
@@ -1713,8 +1711,6 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
         return st;
     if (tasks.empty())
         return IAAT_OK;
-    if (tasks.size() > (size_t)kInline)   // too many pieces for the parameter block
-        return iaat_gemm_grouped_noalloc(&g, 1, esz == 4 ? IAAT_F32 : IAAT_F64, stream);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
@@ -1722,23 +1718,29 @@ static iaat_status_t single_gemm(int esz, int ta, int tb, int M, int N, int K, d
     st = prepare_device(dev, kernel_kind(esz == 4 ? IAAT_F32 : IAAT_F64, IAAT_PREC_DEFAULT));
     if (st != IAAT_OK)
         return st;
-    KParams kp;
-    std::memset(&kp, 0, sizeof kp);
-    for (size_t i = 0; i < tasks.size(); ++i) {
-        kp.inline_tasks[i] = tasks[i].d;
-        kp.inline_gbeg[i] = (int32_t)i;
-    }
-    kp.inline_gbeg[tasks.size()] = (int32_t)tasks.size();
-    kp.p.tasks = nullptr;
-    kp.p.gbeg = nullptr;
-    kp.p.ngroups = (int32_t)tasks.size();
     int32_t *w = nullptr;
     if ((e = single_call_err_ptr(&w)) != cudaSuccess)
         return cuda_fail(e, "cudaGetSymbolAddress");
-    kp.p.err = w;
-    e = launch_fma(esz == 4 ? 0 : 1, kp, (int)tasks.size(), static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess)
-        return cuda_fail(e, "kernel launch");
+    // The pieces travel in the kernel's parameter block, kInline per launch:
+    // an instance cut into more pieces (e.g. 512000 x 1 x 1) takes several
+    // launches on the stream, one after another, and no device memory.
+    for (size_t t0 = 0; t0 < tasks.size(); t0 += kInline) {
+        const size_t n = std::min(tasks.size() - t0, (size_t)kInline);
+        KParams kp;
+        std::memset(&kp, 0, sizeof kp);
+        for (size_t i = 0; i < n; ++i) {
+            kp.inline_tasks[i] = tasks[t0 + i].d;
+            kp.inline_gbeg[i] = (int32_t)i;
+        }
+        kp.inline_gbeg[n] = (int32_t)n;
+        kp.p.tasks = nullptr;
+        kp.p.gbeg = nullptr;
+        kp.p.ngroups = (int32_t)n;
+        kp.p.err = w;
+        e = launch_fma(esz == 4 ? 0 : 1, kp, (int)n, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel launch");
+    }
     return IAAT_OK;
 }
 

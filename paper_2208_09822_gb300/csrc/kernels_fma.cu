@@ -149,6 +149,18 @@ extern "C" iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return noalloc_fail(IAAT_ERR_CUDA, "cudaGetDevice failed");
+    {
+        // the plan reaches the scratch through copies from host arrays that
+        // the next call overwrites: a captured call would replay another
+        // call's tasks, so capture is refused
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess)
+            return noalloc_fail(IAAT_ERR_CUDA, "cudaStreamIsCapturing failed");
+        if (cs != cudaStreamCaptureStatusNone)
+            return noalloc_fail(IAAT_ERR_UNSUPPORTED,
+                                "the allocation-free entry point cannot be captured in a CUDA graph "
+                                "(it copies each call's plan from reused host arrays)");
+    }
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
     if (!g_noalloc_dev[dev]) {
         // set-up, once per device, with that device current

@@ -86,6 +86,58 @@ void apply_text(const std::string &txt, Tuning &t)
     t.from_cache = a || b;
 }
 
+bool read_string(const std::string &txt, const char *key, std::string *dst)
+{
+    std::string k = std::string("\"") + key + "\"";
+    size_t p = txt.find(k);
+    if (p == std::string::npos)
+        return false;
+    p = txt.find(':', p + k.size());
+    if (p == std::string::npos)
+        return false;
+    const size_t a = txt.find('"', p);
+    if (a == std::string::npos)
+        return false;
+    const size_t b = txt.find('"', a + 1);
+    if (b == std::string::npos)
+        return false;
+    *dst = txt.substr(a + 1, b - a - 1);
+    return true;
+}
+
+// The GPU a cache is valid for: name, SM count, compute capability, driver
+// and runtime versions of the current device.
+struct DeviceKey {
+    std::string name;
+    int sms = 0, cc = 0, driver = 0, runtime = 0;
+};
+
+bool current_device_key(DeviceKey *k)
+{
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+        cudaDriverGetVersion(&k->driver) != cudaSuccess || cudaRuntimeGetVersion(&k->runtime) != cudaSuccess)
+        return false;
+    k->name = prop.name;
+    k->sms = prop.multiProcessorCount;
+    k->cc = prop.major * 10 + prop.minor;
+    return true;
+}
+
+// A cache is applied only on the GPU it was measured on: a cache from
+// another GPU, driver or CUDA runtime (or with no key) is ignored.
+bool cache_matches(const std::string &txt)
+{
+    DeviceKey cur, c;
+    if (!current_device_key(&cur))
+        return false;
+    return read_string(txt, "device", &c.name) && read_int(txt, "sm_count", &c.sms, 1, 1 << 20) &&
+           read_int(txt, "compute_capability", &c.cc, 1, 1000) && read_int(txt, "driver_version", &c.driver, 1, 1 << 30) &&
+           read_int(txt, "runtime_version", &c.runtime, 1, 1 << 30) && c.name == cur.name && c.sms == cur.sms &&
+           c.cc == cur.cc && c.driver == cur.driver && c.runtime == cur.runtime;
+}
+
 void load()
 {
     const char *path = std::getenv("IAAT_TUNE_CACHE");
@@ -100,6 +152,8 @@ void load()
     while ((n = std::fread(buf, 1, sizeof buf, f)) > 0)
         txt.append(buf, n);
     std::fclose(f);
+    if (!cache_matches(txt))
+        return;
     Tuning t;
     apply_text(txt, t);
     g_tuning = t;
@@ -343,14 +397,15 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
     }
     const char *path = cache_path ? cache_path : std::getenv("IAAT_TUNE_CACHE");
     if (path && *path) {
-        cudaDeviceProp prop{};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaGetDeviceProperties(&prop, dev);
+        DeviceKey key;
+        if (!current_device_key(&key))
+            return IAAT_ERR_CUDA;
         FILE *f = std::fopen(path, "wb");
         if (!f)
             return IAAT_ERR_INVALID_VALUE;
-        std::fprintf(f, "{\n  \"device\": \"%s\",\n  \"sm_count\": %d,\n", prop.name, prop.multiProcessorCount);
+        std::fprintf(f, "{\n  \"device\": \"%s\",\n  \"sm_count\": %d,\n  \"compute_capability\": %d,\n",
+                     key.name.c_str(), key.sms, key.cc);
+        std::fprintf(f, "  \"driver_version\": %d,\n  \"runtime_version\": %d,\n", key.driver, key.runtime);
         std::fprintf(f, "  \"variant_scale_f32\": [");
         for (int v = 0; v < kNumVariantsF32; ++v)
             std::fprintf(f, "%s%.4f", v ? ", " : "", t.scale_f32[v]);

@@ -53,3 +53,39 @@ def test_autotune_writes_cache_and_tuned_plans_stay_correct(tmp_path):
     env = dict(os.environ, IAAT_TUNE_CACHE=path)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_cache_applies_only_on_the_gpu_it_was_measured_on(tmp_path):
+    """The cache names the GPU, its SM count and compute capability, the
+    driver and the CUDA runtime; a process applies it only when all match.
+    A cache forcing 8 tasks per stage changes the plan's stage count; the
+    same cache with another device name is ignored."""
+    path = str(tmp_path / "tune.json")
+    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, path)
+    cache = json.load(open(path))
+    for key in ("device", "sm_count", "compute_capability", "driver_version", "runtime_version"):
+        assert key in cache, key
+    forced = dict(cache, group_tasks_ffma=8)
+    other = dict(forced, device=cache["device"] + " (another GPU)")
+    paths = {}
+    for name, c in (("forced", forced), ("other", other)):
+        paths[name] = str(tmp_path / f"{name}.json")
+        json.dump(c, open(paths[name], "w"))
+    code = (
+        "import sys; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from paper_2208_09822_gb300 import workloads as W, iaat\n"
+        "from tests.gpu_util import to_device\n"
+        "b = W.uneven(count=3000, seed=5)\n"
+        "tA, tB, tC, d = to_device(b)\n"
+        "print(iaat.iaat_plan_info(iaat.iaat_plan_create(d, iaat.IAAT_F32))['groups'])\n" % (ROOT, ROOT))
+    groups = {}
+    for name in ("forced", "other", None):
+        env = dict(os.environ)
+        env.pop("IAAT_TUNE_CACHE", None)
+        if name:
+            env["IAAT_TUNE_CACHE"] = paths[name]
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        groups[name] = int(r.stdout.strip().splitlines()[-1])
+    assert groups["other"] == groups[None]
+    assert groups["forced"] > groups[None]

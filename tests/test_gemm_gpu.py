@@ -216,9 +216,11 @@ def test_cuda_graph_replay(cuda):
 def test_single_call(cuda, dtype):
     torch = cuda
     rng = np.random.default_rng(31)
+    # the last two need more pieces than one launch's parameter block holds
+    # (32): the call takes several launches on the stream
     shapes = [(1, 1, 1, 0, 0), (17, 23, 9, 1, 0), (80, 80, 80, 0, 0), (32, 32, 32, 1, 0),
               (80, 3, 80, 1, 1), (64, 80, 80, 0, 1), (33, 65, 40, 0, 0), (200, 200, 12, 1, 1),
-              (5000, 100, 1, 0, 1)]
+              (5000, 100, 1, 0, 1), (512000, 1, 1, 0, 0), (1, 512000, 1, 0, 1)]
     for M, N, K, ta, tb in shapes:
         b = W.make_batch([M], [N], [K], [ta], [tb], 0.75, -1.25, dtype, rng, pad=[[1, 2, 3]])
         tA, tB, tC, descs = to_device(b)
