@@ -75,6 +75,25 @@ def make_workload(name, n):
     return getattr(W, gen)(count=n)
 
 
+def shard_ranges(batch, world):
+    """--split shard: the contiguous instance range [i0, i1) of every rank,
+    cut with shard.shard_bounds on shard.instance_cost so that the ranks get
+    about the same work, with each range's flops and the element spans
+    [lo, hi) of its A, B and C in the pools (what the rank copies in and
+    out end to end).  The ranges cover the batch once, in order."""
+    from paper_2208_09822_gb300.shard import instance_cost, shard_bounds
+    cost = instance_cost(batch.M, batch.N, batch.K, batch.beta != 0, batch.esize)
+    n = batch.count
+    out = []
+    for i0, i1 in shard_bounds(cost, world):
+        def span(off, pool):
+            return (int(off[i0]) if i0 < n else pool.size, int(off[i1]) if i1 < n else pool.size)
+        sub = batch.select(np.arange(i0, i1))
+        out.append({"i0": i0, "i1": i1, "flops": sub.flops() if i1 > i0 else 0,
+                    "A": span(batch.offA, batch.A), "B": span(batch.offB, batch.B), "C": span(batch.offC, batch.C)})
+    return out
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -401,6 +420,9 @@ def main():
                     help="time same-size batches on the M = N = K diagonal (prints its own JSON line)")
     ap.add_argument("--pack-ablation", action="store_true",
                     help="time the pack step against the no-pack path by size (prints its own JSON line)")
+    ap.add_argument("--split", default="replicate", choices=["replicate", "shard"],
+                    help="N>1 only: every rank runs the whole batch (replicate, weak scaling; the default) or "
+                         "its contiguous cost-balanced shard of one batch (shard, strong scaling)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the built-in cost model instead of tuning each path first")
     args = ap.parse_args()
@@ -470,6 +492,13 @@ def main():
                           tC.data_ptr() + r * batch.C.nbytes) for r in range(rot)]
     descs = descs_rot[0]
     stream = torch.cuda.Stream(device=dev)
+    # the instances this rank runs: the whole batch, or its shard of it
+    shard = args.split == "shard" and world > 1
+    my = shard_ranges(batch, world)[rank] if shard else \
+        {"i0": 0, "i1": batch.count, "flops": batch.flops(), "A": (0, batch.A.size), "B": (0, batch.B.size),
+         "C": (0, batch.C.size)}
+    r0, r1 = my["i0"], my["i1"]
+    job_flops = batch.flops() if shard else batch.flops() * world   # every rank's instances together
 
     def make_plan(d, name):
         if wl_dtype == 0:
@@ -487,7 +516,7 @@ def main():
         """First launch (kept for the error check), then a CUDA graph of one
         launch per pool copy (one launch when the pools exceed L2) replayed
         between events on the launch stream, `steps` launches in all."""
-        plans = [make_plan(d, name) for d in descs_rot]
+        plans = [make_plan(d[r0:r1], name) for d in descs_rot]
         plan = plans[0]
         info = iaat.iaat_plan_info(plan)
         tC.copy_(C0)
@@ -544,7 +573,7 @@ def main():
     results[args.precision] = (info, ms, first_result)
 
     flops = info["flops"]
-    value = flops * world / (ms * 1e-3) / 1e9
+    value = job_flops / (ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     abytes = info["algorithmic_bytes"]
     achieved = abytes / (ms * 1e-3) / 1e9
@@ -561,15 +590,21 @@ def main():
     hB = torch.from_numpy(batch.B).pin_memory()
     hC = torch.from_numpy(batch.C).pin_memory()
     hOut = torch.empty_like(hC).pin_memory()
-    h2d = hA.numel() * hA.element_size() + hB.numel() * hB.element_size() + hC.numel() * hC.element_size()
-    d2h = hOut.numel() * hOut.element_size()
+    (a0, a1), (b0_, b1_), (c0, c1) = my["A"], my["B"], my["C"]
+    h2d = ((a1 - a0) * hA.element_size() + (b1_ - b0_) * hB.element_size() + (c1 - c0) * hC.element_size())
+    d2h = (c1 - c0) * hOut.element_size()
     args.e2e_steps = max(1, args.e2e_steps)
+
+    def copy_in_out(pl):
+        tA[a0:a1].copy_(hA[a0:a1], non_blocking=True)
+        tB[b0_:b1_].copy_(hB[b0_:b1_], non_blocking=True)
+        tC[c0:c1].copy_(hC[c0:c1], non_blocking=True)
+        iaat.iaat_gemm_grouped(pl, stream)
+        hOut[c0:c1].copy_(tC[c0:c1], non_blocking=True)
 
     def e2e_serial():
         with torch.cuda.stream(stream):
-            tA.copy_(hA, non_blocking=True); tB.copy_(hB, non_blocking=True); tC.copy_(hC, non_blocking=True)
-            iaat.iaat_gemm_grouped(plan, stream)
-            hOut.copy_(tC, non_blocking=True)
+            copy_in_out(plan)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -578,19 +613,15 @@ def main():
         f0.record(stream)
         with torch.cuda.stream(stream):
             for _ in range(args.e2e_steps):
-                tA.copy_(hA, non_blocking=True)
-                tB.copy_(hB, non_blocking=True)
-                tC.copy_(hC, non_blocking=True)
-                iaat.iaat_gemm_grouped(plan, stream)
-                hOut.copy_(tC, non_blocking=True)
+                copy_in_out(plan)
         f1.record(stream)
         torch.cuda.synchronize()
         return f0.elapsed_time(f1) / args.e2e_steps
 
     def e2e_pipelined(nchunks):
         n = batch.count
-        cost = instance_cost(batch.M, batch.N, batch.K, batch.beta != 0)
-        ranges = [(b0, b1) for b0, b1 in shard_bounds(cost, nchunks) if b1 > b0]
+        cost = instance_cost(batch.M[r0:r1], batch.N[r0:r1], batch.K[r0:r1], batch.beta[r0:r1] != 0)
+        ranges = [(r0 + b0, r0 + b1) for b0, b1 in shard_bounds(cost, nchunks) if b1 > b0]
         parts = []
         for b0, b1 in ranges:
             span = lambda off, pool: (int(off[b0]), int(off[b1]) if b1 < n else pool.size)
@@ -642,15 +673,18 @@ def main():
     e2e_serial_ms = e2e_serial()
     iaat.iaat_plan_check(plan, stream)
     e2e_ms, e2e_parts = e2e_pipelined(args.e2e_chunks)
-    # the pipelined result must equal the one-plan result (same inputs, same plans per instance)
-    if rank == 0 and not np.array_equal(hOut.numpy(), first_result):
-        print("warning: pipelined end-to-end result differs from the single launch", file=sys.stderr)
+    # the pipelined result must equal the one-plan result (same inputs, same
+    # plans per instance); a mismatch withholds the end-to-end number
+    e2e_ok = True
+    if rank == 0 and not np.array_equal(hOut.numpy()[c0:c1].view(np.uint8), first_result[c0:c1].view(np.uint8)):
+        e2e_ok = False
+        print("error: pipelined end-to-end result differs from the single launch", file=sys.stderr)
     iaat.iaat_plan_check(plan, stream)
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = flops * world / (e2e_ms * 1e-3) / 1e9
+    e2e_value = job_flops / (e2e_ms * 1e-3) / 1e9
 
     if rank == 0:
         cpu, errs = None, {}
@@ -659,7 +693,7 @@ def main():
         traffic = profile_traffic(args.precision, args.workload, batch.count)
         paths = {}
         for name, (inf, ms_p, _) in results.items():
-            paths[name] = {"value": inf["flops"] * world / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
+            paths[name] = {"value": job_flops / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
                            "ms_per_step": ms_p, "launches_per_step": inf["kernels"],
                            "roofline_frac": inf["algorithmic_bytes"] / (ms_p * 1e-3) / 1e9 / peaks["hbm_gbs"],
                            "error": errs.get(name)}
@@ -679,11 +713,13 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": max(1, args.steps // rot) * rot,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if shard else "weak",
             "vs_baseline": None, "dtype": DTYPE_NAMES[wl_dtype], "data": "synthetic",
             "config": {"workload": wl_desc.format(n=batch.count), "instances": batch.count,
                        "precision": args.precision,
-                       "parallelism": f"instances x{world} (one batch per GPU)",
+                       "parallelism": (f"one batch cut into {world} contiguous cost-balanced shards, one per GPU"
+                                       if shard else f"instances x{world} (one batch per GPU)"),
                        "l2": ("inputs larger than L2 (pools %.2f GB > 129 MB); no flush" % (pool_bytes / 1e9))
                              if rot == 1 else ("pools %.0f MB fit L2: launches rotate over %d copies (%.0f MB); "
                                                "no flush" % (pool_bytes / 1e6, rot, rot * pool_bytes / 1e6)),
@@ -691,7 +727,8 @@ def main():
                        "grid": info["grid"], "tuning": tuned},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e_value if e2e_ok else None, "unit": "GFLOP/s", "ok": e2e_ok,
+                    "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "pipelined_ranges": e2e_parts,
                     "serial_value": flops * world / (e2e_serial_ms * 1e-3) / 1e9},
@@ -705,7 +742,7 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    return 0
+    return 0 if e2e_ok else 1
 
 
 if __name__ == "__main__":

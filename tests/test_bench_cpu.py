@@ -44,3 +44,36 @@ def test_profiles_name_their_sources_and_command():
                                          "grouped_ffma_uneven200k.md": ("ffma",),
                                          "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000)}[name])
         assert (traffic is not None and traffic > 0) == current, name
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_shard_split_bookkeeping(world):
+    """bench.py --split shard: the ranks' instance ranges cover the batch once,
+    in order; their flops add up to the batch's; each rank's pool spans hold
+    exactly the elements of its instances (what it copies end to end); and
+    no rank gets much more than its share of the estimated cost."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    from paper_2208_09822_gb300 import workloads as W
+    from paper_2208_09822_gb300.shard import instance_cost
+    b = W.uneven(count=5000, seed=2)
+    ranges = bench.shard_ranges(b, world)
+    assert len(ranges) == world
+    assert ranges[0]["i0"] == 0 and ranges[-1]["i1"] == b.count
+    for r, s in zip(ranges, ranges[1:]):
+        assert r["i1"] == s["i0"]
+    assert sum(r["flops"] for r in ranges) == b.flops()
+    cost = instance_cost(b.M, b.N, b.K, b.beta != 0, b.esize)
+    for r in ranges:
+        for name, pool in (("A", b.A), ("B", b.B), ("C", b.C)):
+            lo, hi = r[name]
+            rows, cols, ld, off = b.storage(name)
+            idx = np.arange(r["i0"], r["i1"])
+            if len(idx):
+                first = off[idx]
+                last = off[idx] + np.maximum(cols[idx] - 1, 0) * ld[idx] + rows[idx]
+                assert lo <= first.min() and last.max() <= hi
+            assert 0 <= lo <= hi <= pool.size
+        assert cost[r["i0"]:r["i1"]].sum() <= cost.sum() / world + cost.max()

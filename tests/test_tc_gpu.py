@@ -44,11 +44,21 @@ def test_integer_inputs_bit_exact(prec, max_dim):
 
 
 def test_3xbf16_uneven_batch_full():
+    """The full 200,000-instance uneven batch: plain 3xBF16 meets 1e-5 for
+    the batch (its per-instance maximum, reported in the test log, exceeds
+    it at K of 1-2, where the dropped Al*Bl term is not averaged out); the
+    plan that routes K < 8 to FP32 meets 1e-5 for every instance."""
     b = W.uneven()
     C, info = run_grouped(b, iaat.IAAT_PREC_3XBF16)
     err = compare(b, C)
+    print("3xBF16 unrouted, uneven batch:", err)
     assert not err["nan"]
     assert err["eps_batch"] <= 1e-5, err
+    assert padding_untouched(b, C)
+    C, info = run_grouped(b, iaat.IAAT_PREC_3XBF16, route_k_below=8)
+    err = compare(b, C)
+    print("3xBF16 with K < 8 routed to FP32, uneven batch:", err)
+    assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= 1e-5, err
     assert padding_untouched(b, C)
 
 
