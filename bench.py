@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -107,10 +108,37 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
+# the translation unit that holds each path's grouped kernel
+KERNEL_UNITS = {"ffma": "kernels_fma.cu", "dfma": "kernels_fma.cu", "cgemm": "kernels_cplx.cu",
+                "zgemm": "kernels_cplx.cu"}
+
+
+def kernel_unit(precision):
+    base = ROUTE_BASE(precision)
+    stream = precision.endswith("@stream")
+    if base in ("ffma", "dfma"):
+        return "kernels_ws.cu" if stream else KERNEL_UNITS[base]
+    if base in KERNEL_UNITS:
+        return KERNEL_UNITS[base]
+    return "kernels_tc2.cu" if stream else "kernels_tc.cu"
+
+
+def kernel_source_hash(precision="3xbf16"):
+    """Hash of the sources a path's kernel is compiled from: its translation
+    unit and every header it includes (launch.h, which only declares the
+    host launchers, aside), so a profile stays current while that kernel's
+    code is unchanged."""
     csrc = os.path.join(ROOT, "paper_2208_09822_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    seen, todo = set(), [kernel_unit(precision)]
+    while todo:
+        f = todo.pop()
+        if f in seen or f == "launch.h" or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'^#include "([^"/]+)"', fh.read(), re.M)
+    h = hashlib.sha256()
+    for f in sorted(seen):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -129,7 +157,7 @@ def profile_traffic(precision, workload="uneven", count=200_000):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_hash") != kernel_source_hash():
+    if kv.get("kernel_source_hash") != kernel_source_hash(precision):
         return None
     try:
         return float(kv["dram_bytes_per_launch_full"])

@@ -34,15 +34,14 @@ def test_profiles_name_their_sources_and_command():
     the current one, null after any kernel change) and the ncu command."""
     sys.path.insert(0, ROOT)
     import bench
-    h = bench.kernel_source_hash()
     for name in ("grouped_3xbf16_uneven200k.md", "grouped_ffma_uneven200k.md",
                  "grouped_zgemm_uneven-c64100k.md"):
         txt = open(os.path.join(ROOT, "profiles", name)).read()
         assert "kernel_source_hash: " in txt and "ncu --set full --clock-control none" in txt, name
-        current = f"kernel_source_hash: {h}" in txt
-        traffic = bench.profile_traffic(*{"grouped_3xbf16_uneven200k.md": ("3xbf16",),
-                                         "grouped_ffma_uneven200k.md": ("ffma",),
-                                         "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000)}[name])
+        args = {"grouped_3xbf16_uneven200k.md": ("3xbf16",), "grouped_ffma_uneven200k.md": ("ffma",),
+                "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000)}[name]
+        current = f"kernel_source_hash: {bench.kernel_source_hash(args[0])}" in txt
+        traffic = bench.profile_traffic(*args)
         assert (traffic is not None and traffic > 0) == current, name
 
 
