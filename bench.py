@@ -39,10 +39,13 @@ WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT
 NOMINAL_HBM_GBS = 8000.0
 PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4, "3xbf16-k8ffma": 1}
 # each path can also be forced onto one kernel family: name + "@stage"
-# (stage-program kernels) or name + "@stream" (warp-stream / pack-stream)
+# (stage-program kernels), name + "@stream" (warp-stream / pack-stream) or,
+# for the tensor-core paths, name + "@warp" (warp-tile kernel)
 for _n in list(PRECISIONS):
     PRECISIONS[_n + "@stage"] = PRECISIONS[_n + "@stream"] = PRECISIONS[_n]
-KERNEL = {n: (1 if n.endswith("@stage") else 2 if n.endswith("@stream") else 0) for n in PRECISIONS}
+    if PRECISIONS[_n]:
+        PRECISIONS[_n + "@warp"] = PRECISIONS[_n]
+KERNEL = {n: {"stage": 1, "stream": 2, "warp": 3}.get(n.split("@")[1], 0) if "@" in n else 0 for n in PRECISIONS}
 ROUTE_BASE = lambda n: n.split("@")[0]
 # paths that route small-K instances to the FP32 CUDA-core kernel (route_k_below)
 ROUTE = {"3xbf16-k8ffma": 8}
@@ -116,6 +119,8 @@ KERNEL_UNITS = {"ffma": "kernels_fma.cu", "dfma": "kernels_fma.cu", "cgemm": "ke
 def kernel_unit(precision):
     base = ROUTE_BASE(precision)
     stream = precision.endswith("@stream")
+    if precision.endswith("@warp"):
+        return "kernels_tw.cu"
     if base in ("ffma", "dfma"):
         return "kernels_ws.cu" if stream else KERNEL_UNITS[base]
     if base in KERNEL_UNITS:

@@ -137,8 +137,13 @@ typedef struct {
                                   CUDA-core warp-stream kernel, in which every warp
                                   streams its own warp tasks, and the tensor-core
                                   pack-stream kernel, in which four warp groups with a
-                                  producer warp each stream dense 128-row packs).
-                                  FP64 and complex plans always run stage programs */
+                                  producer warp each stream dense 128-row packs),
+                                  3 = the warp-tile tensor-core kernel (tensor-core
+                                  precisions only: every warp stages, converts and
+                                  multiplies its own blocks of at most 32 x 32, op(A)
+                                  from tensor memory; the CUDA-core part of a routed
+                                  plan then takes the default).  FP64 and complex
+                                  plans always run stage programs */
     int32_t reserved[2];
 } iaat_plan_options_t;
 

@@ -283,6 +283,9 @@ struct iaat_plan_s {
     bool ws = false;               // warp-stream kernel (FP32 CUDA-core plans)
     char *d_ws = nullptr;          // its warp tasks, per-warp ranges and error word
     WsParams wsp{};
+    bool tw = false;               // warp-tile tensor-core kernel
+    char *d_tw = nullptr;          // its warp tasks, per-warp ranges and error word
+    TwParams twp{};
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
     iaat_plan_info_t info{};
@@ -297,11 +300,12 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][13];
+bool g_prepared[64][17];
 
 // kind: 0 = FP32 FFMA (stage programs), 1 = FP64 DFMA, 2..5 = tcgen05
 // precision (kind - 1), 6 = complex float, 7 = complex double, 8 = FP32 FFMA
-// warp-stream kernel, 9..12 = pack-stream tensor-core kernel, precision kind - 8
+// warp-stream kernel, 9..12 = pack-stream tensor-core kernel, precision kind - 8,
+// 13..16 = warp-tile tensor-core kernel, precision kind - 12
 iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
@@ -311,6 +315,7 @@ iaat_status_t prepare_device(int dev, int kind)
         cudaError_t e = kind < 2    ? prepare_fma(kind)
                         : kind < 6  ? prepare_tc(kind - 1)
                         : kind == 8 ? prepare_ws()
+                        : kind > 12 ? prepare_tw(kind - 12)
                         : kind > 8  ? prepare_tc2(kind - 8)
                                     : prepare_cplx(kind == 6 ? IAAT_C32 : IAAT_C64);
         if (e != cudaSuccess)
@@ -1308,6 +1313,185 @@ static iaat_status_t plan_create_tc2(const iaat_gemm_desc_t *descs, int64_t coun
 // already rounded to the component type; the descriptors then carry alpha
 // and beta as markers (see make_tasks).  index_map: the caller's index of
 // each descriptor, for error messages (NULL: the position itself).
+// ------------------------------------------ warp-tile tensor-core planner
+// Tensor-core plans with option kernel = 3 run the warp-tile kernel (tw.cuh).
+// Every instance is cut into blocks of at most 32 x 32 of C (rows and columns
+// into near-equal ranges), one warp task each with the instance's whole K;
+// the K range is staged in pieces of kseg values (a multiple of 16), the
+// largest that keep every item of the task within half of a warp's ring.  The
+// tasks are dealt to the warps largest estimated cost first, each to the
+// least loaded warp (warp 0 of every CTA first, then warp 1, ...).
+static double tw_task_cost(int mh, int nw, int K, int ta, int tb, bool readc)
+{
+    // issue slots of one warp, roughly: per task set-up; per 16-value chunk
+    // the row of op(A) per lane, the (row, core row) items of op(B), the MMA
+    // issue and its wait; the epilogue per column; the copies per granule slot
+    const int chunks = K > 0 ? (K + 15) / 16 : 0;
+    const double bsteps = std::ceil((double)nw * 2 / 32.0);
+    double c = 260.0 + chunks * (90.0 + 50.0 * bsteps + 120.0) + 8.0 * nw + 60.0;
+    const double slots = (K > 0 ? (double)tw_a_bytes(ta, mh, K) + (double)tw_b_bytes(tb, nw, K) : 0.0) +
+                         (readc ? (double)tw_c_item_bytes(mh, nw) : 0.0);
+    return c + 16.0 * std::ceil(slots / 16.0 / 32.0);
+}
+
+static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count, iaat_precision_t precision,
+                                    const iaat_plan_options_t *opts, iaat_plan_t *out, const int64_t *index_map)
+{
+    const uint32_t cap = (uint32_t)tw_ring_bytes((int)precision) / 2;
+    std::vector<TwTask> tasks;
+    std::vector<double> cost;
+    tasks.reserve((size_t)count * 2);
+    cost.reserve((size_t)count * 2);
+    iaat_plan_info_t info{};
+    info.instances = count;
+    info.dtype = IAAT_F32;
+    info.precision = precision;
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        const int64_t gi = index_map ? index_map[i] : i;
+        iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+                                          g.alpha, 4);
+        if (st != IAAT_OK)
+            return st;
+        const int M = g.M, N = g.N;
+        if (M == 0 || N == 0)
+            continue;
+        const int K = (g.alpha == 0.0) ? 0 : g.K;
+        if (K == 0 && g.beta == 1.0)
+            continue;   // C = 1*C: nothing to do
+        const bool readc = g.beta != 0.0;
+        info.active += 1;
+        info.flops += 2 * (int64_t)M * N * K;
+        info.algorithmic_bytes += ((int64_t)M * K + (int64_t)K * N + (int64_t)M * N + (readc ? (int64_t)M * N : 0)) * 4;
+        const int nbm = (M + kTwBlock - 1) / kTwBlock, nbn = (N + kTwBlock - 1) / kTwBlock;
+        for (int bj = 0; bj < nbn; ++bj) {
+            int c0, nw;
+            piece_range(N, nbn, bj, c0, nw);
+            for (int bi = 0; bi < nbm; ++bi) {
+                int r0, mh;
+                piece_range(M, nbm, bi, r0, mh);
+                int kseg = 16;
+                if (K > 0) {
+                    kseg = std::min(((K + 15) / 16) * 16, 16 * 255);
+                    while (kseg > 16 && tw_ab_item_bytes(g.transA, g.transB, mh, nw, std::min(K, kseg), true) > cap)
+                        kseg -= 16;
+                }
+                if (tw_ab_item_bytes(g.transA, g.transB, mh, nw, std::min(K, kseg), true) > cap ||
+                    tw_c_item_bytes(mh, nw) > cap)
+                    return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: a block does not fit the staging ring",
+                                (long long)gi);
+                TwTask t{};
+                if (K > 0) {
+                    t.A = static_cast<const char *>(g.A) + (size_t)(g.transA ? (int64_t)r0 * g.lda : (int64_t)r0) * 4;
+                    t.B = static_cast<const char *>(g.B) + (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * 4;
+                }
+                t.C = static_cast<char *>(g.C) + (size_t)((int64_t)r0 + (int64_t)c0 * g.ldc) * 4;
+                t.lda = g.lda;
+                t.ldb = g.ldb;
+                t.ldc = g.ldc;
+                t.K = K;
+                t.M = (int16_t)mh;
+                t.N = (int16_t)nw;
+                t.ta = (uint8_t)g.transA;
+                t.tb = (uint8_t)g.transB;
+                t.flags = readc ? kFlagReadC : 0;
+                t.kseg16 = (uint8_t)(kseg / 16);
+                t.alpha = (float)g.alpha;
+                t.beta = (float)g.beta;
+                tasks.push_back(t);
+                cost.push_back(tw_task_cost(mh, nw, K, g.transA, g.transB, readc));
+            }
+        }
+    }
+
+    iaat_plan_s *plan = new (std::nothrow) iaat_plan_s;
+    if (!plan)
+        return fail(IAAT_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e != cudaSuccess) {
+        delete plan;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    iaat_status_t ps = prepare_device(plan->device, 12 + (int)precision);
+    if (ps != IAAT_OK) {
+        delete plan;
+        return ps;
+    }
+    plan->tw = true;
+    plan->esz = 4;
+    plan->dtype = IAAT_F32;
+    plan->precision = precision;
+    const int64_t nt = (int64_t)tasks.size();
+    const int sms = sm_count(plan->device);
+    const int grid = (int)std::min<int64_t>(nt, (int64_t)sms);
+    const int nwarps = grid * kTwWarps;
+
+    std::vector<int32_t> wbeg((size_t)nwarps + 1, 0);
+    std::vector<TwTask> flat((size_t)nt);
+    if (nt > 0) {
+        std::vector<int32_t> order((size_t)nt);
+        for (int64_t k = 0; k < nt; ++k)
+            order[(size_t)k] = (int32_t)k;
+        std::stable_sort(order.begin(), order.end(), [&cost](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+        using Slot = std::pair<double, int32_t>;   // (load, rank of the warp)
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int r = 0; r < nwarps; ++r)
+            heap.push(Slot(0.0, r));
+        std::vector<int32_t> owner((size_t)nt);
+        std::vector<int32_t> per((size_t)nwarps, 0);
+        for (int32_t k : order) {
+            Slot s = heap.top();
+            heap.pop();
+            const int r = s.second;
+            const int w = (r % grid) * kTwWarps + r / grid;   // CTA r % grid, warp r / grid
+            owner[(size_t)k] = w;
+            ++per[(size_t)w];
+            s.first += cost[(size_t)k];
+            heap.push(s);
+        }
+        for (int w = 0; w < nwarps; ++w)
+            wbeg[(size_t)w + 1] = wbeg[(size_t)w] + per[(size_t)w];
+        std::vector<int32_t> fill(wbeg.begin(), wbeg.end() - 1);
+        for (int32_t k : order)
+            flat[(size_t)fill[(size_t)owner[(size_t)k]]++] = tasks[(size_t)k];
+        if (opts && opts->inject_fault == 1)
+            flat[0].M = 33;   // a record the kernel must refuse
+    }
+    const size_t tb = (size_t)std::max<int64_t>(nt, 1) * sizeof(TwTask);
+    const size_t wb = (((size_t)nwarps + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+    if ((e = cudaMalloc(&plan->d_tw, tb + wb + 256)) != cudaSuccess) {
+        plan->d_tw = nullptr;
+        iaat_plan_destroy(plan);
+        return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
+    }
+    if ((nt > 0 && (e = cudaMemcpy(plan->d_tw, flat.data(), (size_t)nt * sizeof(TwTask), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess) ||
+        (e = cudaMemcpy(plan->d_tw + tb, wbeg.data(), ((size_t)nwarps + 1) * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(plan->d_tw + tb + wb, 0, sizeof(int32_t))) != cudaSuccess) {
+        iaat_plan_destroy(plan);
+        return cuda_fail(e, "upload the warp tasks");
+    }
+    plan->twp.tasks = reinterpret_cast<const TwTask *>(plan->d_tw);
+    plan->twp.wbeg = reinterpret_cast<const int32_t *>(plan->d_tw + tb);
+    plan->twp.err = reinterpret_cast<int32_t *>(plan->d_tw + tb + wb);
+    plan->twp.nwarps = nwarps;
+    plan->d_err = plan->twp.err;
+    plan->ntasks = nt;
+    plan->ngroups = nt > 0 ? nwarps : 0;
+    plan->grid = grid;
+    info.tasks = nt;
+    info.groups = plan->ngroups;
+    info.blocks = nt;
+    info.plan_bytes = (int64_t)(tb + wb + 256);
+    info.grid = grid;
+    info.kernels = nt > 0 ? 1 : 0;
+    plan->info = info;
+    *out = plan;
+    return IAAT_OK;
+}
+
+
 static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t count, int dt,
                                       iaat_precision_t precision, const iaat_plan_options_t *opts,
                                       const double *cscal, iaat_plan_t *out, const int64_t *index_map = nullptr)
@@ -1341,8 +1525,12 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     }
     (void)ctas_per_sm;
     const int kernel = opts ? opts->kernel : 0;
-    if (kernel < 0 || kernel > 2)
+    if (kernel < 0 || kernel > 3)
         return fail(IAAT_ERR_INVALID_VALUE, "kernel %d out of range", kernel);
+    if (kernel == 3 && !tc)
+        return fail(IAAT_ERR_INVALID_VALUE, "kernel 3 (warp-tile tensor-core kernel) needs a tensor-core precision");
+    if (tc && kernel == 3)
+        return plan_create_tw(descs, count, precision, opts, out, index_map);
     if (dt == IAAT_F32 && !tc && kernel == 2)
         return plan_create_ws(descs, count, opts, force_variant, out, index_map);
     if (tc && kernel == 2)
@@ -1521,6 +1709,8 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     if (st != IAAT_OK)
         return st;
     o.inject_fault = 0;
+    if (o.kernel == 3)
+        o.kernel = 0;   // the CUDA-core part has no warp-tile kernel: its default plan
     st = plan_create_impl(dfma.data(), (int64_t)dfma.size(), IAAT_F32, IAAT_PREC_DEFAULT, &o, nullptr, &sub,
                           ifma.data());
     if (st != IAAT_OK) {
@@ -1577,10 +1767,11 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
         return fail(IAAT_ERR_INVALID_VALUE, "plan is NULL");
     if (plan->ngroups == 0)
         return plan->sub ? iaat_gemm_grouped(plan->sub, stream) : IAAT_OK;
-    if (plan->ws || plan->tc2) {
-        const cudaError_t e = plan->ws ? launch_ws(plan->wsp, plan->grid, static_cast<cudaStream_t>(stream))
-                                       : launch_tc2((int)plan->precision, plan->t2p, plan->grid,
-                                                    static_cast<cudaStream_t>(stream));
+    if (plan->ws || plan->tc2 || plan->tw) {
+        const cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const cudaError_t e = plan->ws    ? launch_ws(plan->wsp, plan->grid, s)
+                              : plan->tw ? launch_tw((int)plan->precision, plan->twp, plan->grid, s)
+                                         : launch_tc2((int)plan->precision, plan->t2p, plan->grid, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel launch");
         if (plan->sub)   // routed small-K instances, after the tensor-core launch on the same stream
@@ -1668,10 +1859,12 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
         cudaFree(plan->d_prog);
     if (plan->d_poff)
         cudaFree(plan->d_poff);
-    if (plan->d_err && !plan->ws)
+    if (plan->d_err && !plan->ws && !plan->tw)
         cudaFree(plan->d_err);
     if (plan->d_ws)
         cudaFree(plan->d_ws);
+    if (plan->d_tw)
+        cudaFree(plan->d_tw);
     if (plan->d_gbeg)
         cudaFree(plan->d_gbeg);
     if (plan->d_scal)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "tw_types.cuh"
 #include "../../include/iaat.h"
 
 namespace iaat {
@@ -20,6 +21,10 @@ int tc_group_cap(int precision);        // largest stage footprint (bytes)
 cudaError_t prepare_tc2(int precision);
 cudaError_t launch_tc2(int precision, const Tc2Params &p, int grid, cudaStream_t stream);
 int tc2_ring_bytes(int precision);      // staging ring of one warp group (bytes)
+// warp-tile tensor-core kernel (tw.cuh)
+cudaError_t prepare_tw(int precision);
+cudaError_t launch_tw(int precision, const TwParams &p, int grid, cudaStream_t stream);
+int tw_ring_bytes(int precision);       // staging ring of one warp (bytes)
 // complex kernel (CGEMM / ZGEMM), dtype IAAT_C32 or IAAT_C64
 cudaError_t prepare_cplx(int dtype);
 cudaError_t launch_cplx(int dtype, const KParams &kp, int grid, cudaStream_t stream);

@@ -180,8 +180,9 @@ class Plan:
 
 def iaat_plan_create(descs, dtype, precision=IAAT_PREC_DEFAULT, *, max_group_tasks=0, force_variant=0,
                      inject_fault=0, route_k_below=0, kernel=0):
-    """descs: numpy array of DESC_DTYPE (device pointers inside).  kernel:
-    FP32 CUDA-core plans only, 0 = warp-stream kernel, 1 = stage-program kernel."""
+    """descs: numpy array of DESC_DTYPE (device pointers inside).  kernel
+    (iaat_plan_options_t.kernel): 0 = default, 1 = stage-program kernels,
+    2 = stream kernels, 3 = warp-tile tensor-core kernel."""
     descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
     opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault, route_k_below, kernel)
     h = ctypes.c_void_p()
