@@ -37,7 +37,9 @@ def test_profiles_name_their_sources_and_command():
     for name in ("grouped_3xbf16_uneven200k.md", "grouped_ffma_uneven200k.md",
                  "grouped_zgemm_uneven-c64100k.md"):
         txt = open(os.path.join(ROOT, "profiles", name)).read()
-        assert "kernel_source_hash: " in txt and "ncu --set full --clock-control none" in txt, name
+        ncu = [ln for ln in txt.splitlines() if ln.startswith("ncu ")]
+        assert "kernel_source_hash: " in txt and ncu, name
+        assert all("--clock-control none" in ln and "--set full" in ln for ln in ncu), name
         args = {"grouped_3xbf16_uneven200k.md": ("3xbf16",), "grouped_ffma_uneven200k.md": ("ffma",),
                 "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000)}[name]
         current = f"kernel_source_hash: {bench.kernel_source_hash(args[0])}" in txt

@@ -105,14 +105,14 @@ def test_instances_cut_into_blocks(prec):
 
 @pytest.mark.parametrize("prec", ["3xbf16", "tf32"])
 def test_long_k_in_several_items(prec):
-    """1 x 1 x K up to the domain's bound and 32 x 32 x 500: K staged in
-    several ring items, accumulated across them; integer entries keep every
-    partial sum exact."""
+    """1 x 1 x K up to the domain's bound, 32 x 32 x 500 and a TN block of
+    K = 36: K staged in several ring items, accumulated across them; integer
+    entries keep every partial sum exact."""
     rng = np.random.default_rng(5)
-    K = [20000, 512000, 40000, 500, 480]
-    b = W.make_batch([1, 1, 2, 32, 30], [1, 1, 3, 32, 31], K, [0, 0, 0, 1, 0], [1, 1, 0, 0, 1],
-                     [1.0, -0.5, 2.0, 1.0, -1.0], [0.5, 0.0, 1.0, 0.0, 2.0], np.float32, rng,
-                     pad=np.zeros((5, 3), np.int64), dist="int")
+    K = [20000, 512000, 40000, 500, 480, 36]
+    b = W.make_batch([1, 1, 2, 32, 30, 30], [1, 1, 3, 32, 31, 30], K, [0, 0, 0, 0, 0, 1], [1, 1, 0, 0, 1, 0],
+                     [1.0, -0.5, 2.0, 1.0, -1.0, 1.0], [0.5, 0.0, 1.0, 0.0, 2.0, -1.0], np.float32, rng,
+                     pad=np.zeros((6, 3), np.int64), dist="int")
     assert W.in_domain(b.M, b.N, b.K, b.transA, b.transB).all()
     C, info = run_grouped(b, PRECS[prec], kernel=WARP)
     err = compare(b, C)
