@@ -1315,23 +1315,31 @@ static iaat_status_t plan_create_tc2(const iaat_gemm_desc_t *descs, int64_t coun
 // each descriptor, for error messages (NULL: the position itself).
 // ------------------------------------------ warp-tile tensor-core planner
 // Tensor-core plans with option kernel = 3 run the warp-tile kernel (tw.cuh).
-// Every instance is cut into blocks of at most 32 x 32 of C (rows and columns
-// into near-equal ranges), one warp task each with the instance's whole K;
+// Every instance is cut into blocks of at most kTwBlockM x kTwBlockN of C
+// (rows and columns into near-equal ranges), one warp task each with the instance's whole K;
 // the K range is staged in pieces of kseg values (a multiple of 16), the
 // largest that keep every item of the task within half of a warp's ring.  The
 // tasks are dealt to the warps largest estimated cost first, each to the
 // least loaded warp (warp 0 of every CTA first, then warp 1, ...).
-static double tw_task_cost(int mh, int nw, int K, int ta, int tb, bool readc)
+static double tw_task_cost(const TwTask &t)
 {
     // issue slots of one warp, roughly: per task set-up; per 16-value chunk
     // the row of op(A) per lane, the (row, core row) items of op(B), the MMA
     // issue and its wait; the epilogue per column; the copies per granule slot
+    const int K = t.K, nw = t.N;
     const int chunks = K > 0 ? (K + 15) / 16 : 0;
     const double bsteps = std::ceil((double)nw * 2 / 32.0);
     double c = 260.0 + chunks * (90.0 + 50.0 * bsteps + 120.0) + 8.0 * nw + 60.0;
-    const double slots = (K > 0 ? (double)tw_a_bytes(ta, mh, K) + (double)tw_b_bytes(tb, nw, K) : 0.0) +
-                         (readc ? (double)tw_c_item_bytes(mh, nw) : 0.0);
+    const double slots = (K > 0 ? (double)tw_ab_item_bytes(t, K, false) : 0.0) +
+                         ((t.flags & kFlagReadC) ? (double)tw_c_item_bytes(t) : 0.0);
     return c + 16.0 * std::ceil(slots / 16.0 / 32.0);
+}
+
+// Stage an operand block as one span when that takes no more ring bytes
+// than staging it run by run.
+static bool tw_span(int runs, int len, int64_t ld)
+{
+    return tw_op_bytes(runs, len, ld, true) <= tw_op_bytes(runs, len, ld, false);
 }
 
 static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count, iaat_precision_t precision,
@@ -1363,23 +1371,13 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
         info.active += 1;
         info.flops += 2 * (int64_t)M * N * K;
         info.algorithmic_bytes += ((int64_t)M * K + (int64_t)K * N + (int64_t)M * N + (readc ? (int64_t)M * N : 0)) * 4;
-        const int nbm = (M + kTwBlock - 1) / kTwBlock, nbn = (N + kTwBlock - 1) / kTwBlock;
+        const int nbm = (M + kTwBlockM - 1) / kTwBlockM, nbn = (N + kTwBlockN - 1) / kTwBlockN;
         for (int bj = 0; bj < nbn; ++bj) {
             int c0, nw;
             piece_range(N, nbn, bj, c0, nw);
             for (int bi = 0; bi < nbm; ++bi) {
                 int r0, mh;
                 piece_range(M, nbm, bi, r0, mh);
-                int kseg = 16;
-                if (K > 0) {
-                    kseg = std::min(((K + 15) / 16) * 16, 16 * 255);
-                    while (kseg > 16 && tw_ab_item_bytes(g.transA, g.transB, mh, nw, std::min(K, kseg), true) > cap)
-                        kseg -= 16;
-                }
-                if (tw_ab_item_bytes(g.transA, g.transB, mh, nw, std::min(K, kseg), true) > cap ||
-                    tw_c_item_bytes(mh, nw) > cap)
-                    return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: a block does not fit the staging ring",
-                                (long long)gi);
                 TwTask t{};
                 if (K > 0) {
                     t.A = static_cast<const char *>(g.A) + (size_t)(g.transA ? (int64_t)r0 * g.lda : (int64_t)r0) * 4;
@@ -1394,12 +1392,31 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
                 t.N = (int16_t)nw;
                 t.ta = (uint8_t)g.transA;
                 t.tb = (uint8_t)g.transB;
-                t.flags = readc ? kFlagReadC : 0;
-                t.kseg16 = (uint8_t)(kseg / 16);
                 t.alpha = (float)g.alpha;
                 t.beta = (float)g.beta;
+                // the K range per item (kseg, a multiple of 16): the largest
+                // that keeps every item of the task within half the ring; the
+                // span-or-runs choice of op(A) and op(B) depends on it
+                // (transposed operands' runs are the item's K range long)
+                int kseg = K > 0 ? std::min(((K + 15) / 16) * 16, 16 * 255) : 16;
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int kl = std::min(K, kseg);
+                    t.flags = (uint8_t)((readc ? kFlagReadC : 0) | (tw_span(nw, mh, g.ldc) ? kTwSpanC : 0));
+                    if (K > 0) {
+                        if (g.transA ? tw_span(mh, kl, g.lda) : tw_span(kl, mh, g.lda))
+                            t.flags |= kTwSpanA;
+                        if (g.transB ? tw_span(kl, nw, g.ldb) : tw_span(nw, kl, g.ldb))
+                            t.flags |= kTwSpanB;
+                        while (kseg > 16 && tw_ab_item_bytes(t, std::min(K, kseg), true) > cap)
+                            kseg -= 16;
+                    }
+                }
+                t.kseg16 = (uint8_t)(kseg / 16);
+                if (tw_ab_item_bytes(t, std::min(K, kseg), true) > cap || tw_c_item_bytes(t) > cap)
+                    return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: a block does not fit the staging ring",
+                                (long long)gi);
                 tasks.push_back(t);
-                cost.push_back(tw_task_cost(mh, nw, K, g.transA, g.transB, readc));
+                cost.push_back(tw_task_cost(t));
             }
         }
     }

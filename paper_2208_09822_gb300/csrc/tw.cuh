@@ -4,14 +4,16 @@
 // every warp its own pipeline.
 //
 // The planner cuts every instance into warp tasks -- blocks of at most
-// 32 x 32 of C, each with the instance's whole K -- and deals them to the
-// warps of the grid ahead of time, largest first, each to the least loaded
-// warp.  A warp then runs its list alone; no other warp waits for it:
+// kTwBlockM x kTwBlockN (32 x 32) of C, each with the instance's whole K --
+// and deals them to the warps of the grid ahead of time, largest first, each
+// to the least loaded warp.  A warp then runs its list alone; no other warp
+// waits for it:
 //
 //  * staging: the warp's lanes copy each task's raw operands into the warp's
 //    private ring with 16-byte cp.async (L2 to shared memory), as runs --
 //    the contiguous stretches of the stored columns, each as the 16-byte
-//    granules that cover it -- cut by K into items that fit half the ring,
+//    granules that cover it -- or, where the ld padding is small, as one span
+//    over all of them, cut by K into items that fit half the ring,
 //    up to kTwMaxOut items ahead of the one being computed, each item one
 //    cp.async group;
 //  * convert, per K-chunk of 16: lane i turns row i of the block's op(A)
@@ -44,13 +46,13 @@ namespace iaat {
 template <int P> IAAT_CE int tw_vpr() { return 16 / TcTraits<P>::kOpBytes; }       // values per core row
 template <int P> IAAT_CE int tw_groups() { return kTwKC / tw_vpr<P>(); }          // core rows per tile row
 template <int P> IAAT_CE int tw_sbo() { return tw_groups<P>() * 128; }            // 8-row group stride
-template <int P> IAAT_CE int tw_tile() { return (kTwBlock / 8) * tw_sbo<P>(); }   // 32 rows of B, one term
+template <int P> IAAT_CE int tw_tile() { return (kTwBlockN / 8) * tw_sbo<P>(); }  // the rows of op(B)^T, one term
 template <int P> IAAT_CE int tw_region() { return kTwWarps * tw_tile<P>(); }      // one term of every warp
 // tensor-memory columns of one chunk of op(A), one term (32-bit columns)
 template <int P> IAAT_CE int tw_acols() { return kTwKC * TcTraits<P>::kOpBytes / 4; }
-// tensor memory: the warps' accumulators (32 columns each), then per quad of
-// warps the A columns of every term
-constexpr int kTwAccCols = 32 * kTwWarps;
+// tensor memory: the warps' accumulators (kTwBlockN columns each), then per
+// quad of warps the A columns of every term
+constexpr int kTwAccCols = kTwBlockN * kTwWarps;
 template <int P> IAAT_CE int tw_tmem_cols() { return kTwAccCols + (kTwWarps / 4) * TcTraits<P>::kTerms * tw_acols<P>(); }
 constexpr uint32_t kTwTmemAlloc = 512;
 // shared memory: the warps' mbarriers and the tensor-memory slot, then the
@@ -59,7 +61,8 @@ constexpr int kTwCtl = 1024;
 template <int P> IAAT_CE int tw_opB() { return kTwCtl; }
 template <int P> IAAT_CE int tw_ring_off() { return kTwCtl + TcTraits<P>::kTerms * tw_region<P>(); }
 template <int P> IAAT_CE int tw_ring() { return ((kSmemTotal - tw_ring_off<P>()) / kTwWarps) & ~127; }
-static_assert(kTwWarps % 4 == 0, "quads of warps");
+static_assert(kTwWarps % 4 == 0 && kTwBlockM == 32 && (kTwBlockN == 16 || kTwBlockN == 32),
+              "quads of warps, one lane quarter per block, MMA N of 16 or 32");
 static_assert(tw_tmem_cols<kTc6xBF16>() <= (int)kTwTmemAlloc && tw_tmem_cols<kTcTF32>() <= (int)kTwTmemAlloc,
               "tensor-memory columns");
 static_assert(kTwMaxOut == 8, "queue slots in lanes 0..7, cp.async groups");
@@ -73,13 +76,14 @@ constexpr uint32_t kTwEpi = 4;     // the block's epilogue follows this item
 // (D = tw_run_slot(X)), so its first element lands at dst + r*D +
 // ((src + r*S) & 15).  Lane e of every 32 takes granule slot e: run
 // floor(e / L), granule e mod L (L = D / 16), the quotient taken in FP32 --
-// exact: (e + 1/2) / L is at least 1/(2L) from an integer and the product's
-// relative error is below 2^-23, so for e < 2^22 the floor is right.
+// exact: (e + 1/2) / L is at least 1/(2L) from an integer, and with a
+// reciprocal good to 2 ulp the product's relative error stays below 2^-21,
+// so for e < 2^20 the floor is right.
 __device__ __forceinline__ void tw_copy_runs(uint32_t dst, const char *src, int64_t S, int R, int X, int lane)
 {
     const int L = (X + 27) >> 4;
     const int n = R * L;
-    const float inv = 1.0f / (float)L;
+    const float inv = __fdividef(1.0f, (float)L);
     for (int e = lane; e < n; e += 32) {
         const int r = (int)(((float)e + 0.5f) * inv);
         const int g = e - r * L;
@@ -90,11 +94,35 @@ __device__ __forceinline__ void tw_copy_runs(uint32_t dst, const char *src, int6
     }
 }
 
+// Copy `bytes` bytes from global address src as the 16-byte granules that
+// cover them, to dst (the first byte lands at dst + (src & 15)).
+__device__ __forceinline__ void tw_copy_span(uint32_t dst, const char *src, int64_t bytes, int lane)
+{
+    const uintptr_t s = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t a = s & ~(uintptr_t)15;
+    const int n = (int)(((int64_t)(s & 15u) + bytes + 15) >> 4);
+    for (int e = lane; e < n; e += 32)
+        cp_async16(dst + 16u * (uint32_t)e, reinterpret_cast<const void *>(a + 16u * (uint32_t)e));
+}
+
+// Stage one operand block: R runs of len elements, ld elements apart, the
+// first at src; as one span or run by run (tw_op_bytes).
+__device__ __forceinline__ void tw_copy_op(uint32_t dst, const char *src, int64_t ld, int R, int len, bool span,
+                                           int lane)
+{
+    if (R <= 0 || len <= 0)
+        return;
+    if (span)
+        tw_copy_span(dst, src, 4 * ((int64_t)(R - 1) * ld + len), lane);
+    else
+        tw_copy_runs(dst, src, 4 * ld, R, 4 * len, lane);
+}
+
 // The task the warp is computing, from the record at the start of its first item.
 struct TwCur {
     const char *A, *B;
     float *C;
-    int lda, ldb, ldc, K, M, N, ta, tb, readc;
+    int lda, ldb, ldc, K, M, N, ta, tb, readc, flags;
     float alpha, beta;
 };
 
@@ -114,6 +142,7 @@ __device__ __forceinline__ TwCur tw_read_record(const char *rec)
     c.ta = t.ta;
     c.tb = t.tb;
     c.readc = (t.flags & kFlagReadC) != 0;
+    c.flags = t.flags;
     c.alpha = t.alpha;
     c.beta = t.beta;
     return c;
@@ -122,9 +151,11 @@ __device__ __forceinline__ TwCur tw_read_record(const char *rec)
 // Staged operand geometry of one item.  krun: the stored runs go along k (one
 // per k), element (row, k) at sec + k*D + mis(k) + 4*row; otherwise one run
 // per row, element (row, k) at sec + row*D + mis(row) + 4*k; mis(r) =
-// (b0 + r*s16) & 15, k relative to the item's K range.  Chunks and core rows
-// start at multiples of 4 runs, and 4*s16 is a multiple of 16, so the offsets
-// of the values of a core row repeat from one to the next.
+// (b0 + r*s16) & 15, k relative to the item's K range.  Staged run by run:
+// D = tw_run_slot(4 len), s16 = 4 ld mod 16; as one span: D = 4 ld, s16 = 0.
+// Chunks and core rows start at multiples of 4 runs, and 4*s16 is a multiple
+// of 16, so the offsets of the values of a core row repeat from one to the
+// next.
 struct TwSide {
     const char *sec;
     int D, b0, s16;
@@ -227,6 +258,7 @@ __device__ __forceinline__ void tw_convert_b(const TwSide &s, int rows, int kc, 
     for (int v = 0; v < V; ++v)
         o[v] = s.krun ? v * s.D + ((s.b0 + v * s.s16) & 15) : 4 * v;
     const int n = rows * G;
+#pragma unroll 2
     for (int e = lane; e < n; e += 32) {
         const int row = e >> LG, g = e & (G - 1);
         const int k = kc + g * V;   // first k of this core row
@@ -302,7 +334,7 @@ __device__ __forceinline__ void tw_mma(uint32_t at, uint32_t bw, uint32_t dtmem,
 }
 
 // Lane i (< M) writes row i of the block: alpha*acc + beta*C0, C0 from the
-// staged C item (one run per column, runs of tw_run_slot(4M) bytes).
+// staged C item (one run per column, or one span).
 __device__ __forceinline__ void tw_epilogue(const TwCur &t, const char *citem, uint32_t taddr, bool product, int nt,
                                             int lane)
 {
@@ -322,29 +354,42 @@ __device__ __forceinline__ void tw_epilogue(const TwCur &t, const char *citem, u
     float *cp = t.C + lane;
     const int64_t ldc = t.ldc;
     if (t.readc) {
-        const int DC = (int)tw_run_slot(4 * t.M);
-        const int c0 = (int)(reinterpret_cast<uintptr_t>(t.C) & 15u), s16 = (int)((4 * ldc) & 15);
+        const bool span = (t.flags & kTwSpanC) != 0;
+        const int DC = span ? (int)(4 * ldc) : (int)tw_run_slot(4 * t.M);
+        const int c0 = (int)(reinterpret_cast<uintptr_t>(t.C) & 15u), s16 = span ? 0 : (int)((4 * ldc) & 15);
         int mis[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             mis[u] = (c0 + u * s16) & 15;
         const char *sp = citem + 4 * lane;
+        // eight columns at a time: their C0 loads issue together
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j >= t.N)
+        for (int j0 = 0; j0 < 32; j0 += 8) {
+            if (j0 >= t.N)
                 break;
-            const float c = *reinterpret_cast<const float *>(sp + mis[j & 3]);
-            __stcs(cp, fmaf(t.beta, c, t.alpha * __uint_as_float(acc[j])));
-            cp += ldc;
-            sp += DC;
+            float c[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                c[u] = j0 + u < t.N ? *reinterpret_cast<const float *>(sp + u * DC + mis[u & 3]) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (j0 + u < t.N)
+                    __stcs(cp, fmaf(t.beta, c[u], t.alpha * __uint_as_float(acc[j0 + u])));
+                cp += ldc;
+            }
+            sp += 8 * DC;
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j >= t.N)
+        for (int j0 = 0; j0 < 32; j0 += 8) {
+            if (j0 >= t.N)
                 break;
-            __stcs(cp, t.alpha * __uint_as_float(acc[j]));
-            cp += ldc;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (j0 + u < t.N)
+                    __stcs(cp, t.alpha * __uint_as_float(acc[j0 + u]));
+                cp += ldc;
+            }
         }
     }
 }
@@ -371,7 +416,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 512);
     const uint32_t lq = (uint32_t)(32 * q) << 16;                              // the warp's lane quarter
-    const uint32_t dcol = tmem + 32u * (uint32_t)warp;                         // its accumulator (MMA D)
+    const uint32_t dcol = tmem + (uint32_t)(kTwBlockN * warp);                 // its accumulator (MMA D)
     const uint32_t acol = tmem + (uint32_t)(kTwAccCols + (warp >> 2) * T * tw_acols<P>());   // its quad's A
     char *tB0 = smem + tw_opB<P>() + warp * tw_tile<P>();
     char *tB1 = tB0 + tw_region<P>(), *tB2 = tB1 + tw_region<P>();
@@ -390,32 +435,33 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
     // issue side: the record of the task being staged (word l in lane l < 16)
     // and the next three, prefetched
     uint32_t rw = load_rec(it), r1 = load_rec(it + 1), r2 = load_rec(it + 2), r3 = load_rec(it + 3);
-    const char *iA = nullptr, *iB = nullptr, *iC = nullptr;
-    int ilda = 0, ildb = 0, ildc = 0, iK = 0, iM = 0, iN = 0, ita = 0, itb = 0, ireadc = 0, ikseg = 16, inseg = 1,
-        iseg = 0;
+    TwTask ir{};   // the task being staged
+    int ireadc = 0, ikseg = 16, inseg = 1, iseg = 0;
     // decode rw; false (and the error word set) for a record the kernel must refuse
     auto begin = [&]() -> bool {
         auto F = [&](int w) { return __shfl_sync(0xffffffffu, rw, w); };
-        iA = reinterpret_cast<const char *>(((uint64_t)F(1) << 32) | F(0));
-        iB = reinterpret_cast<const char *>(((uint64_t)F(3) << 32) | F(2));
-        iC = reinterpret_cast<const char *>(((uint64_t)F(5) << 32) | F(4));
-        ilda = (int)F(6);
-        ildb = (int)F(7);
-        ildc = (int)F(8);
-        iK = (int)F(9);
+        ir.A = reinterpret_cast<const char *>(((uint64_t)F(1) << 32) | F(0));
+        ir.B = reinterpret_cast<const char *>(((uint64_t)F(3) << 32) | F(2));
+        ir.C = reinterpret_cast<char *>(((uint64_t)F(5) << 32) | F(4));
+        ir.lda = (int)F(6);
+        ir.ldb = (int)F(7);
+        ir.ldc = (int)F(8);
+        ir.K = (int)F(9);
         const uint32_t mn = F(10), w11 = F(11);
-        iM = (int)(int16_t)(mn & 0xffffu);
-        iN = (int)(int16_t)(mn >> 16);
-        ita = (int)(w11 & 0xffu);
-        itb = (int)((w11 >> 8) & 0xffu);
-        ireadc = (int)((w11 >> 16) & kFlagReadC);
-        ikseg = 16 * (int)(w11 >> 24);
+        ir.M = (int16_t)(mn & 0xffffu);
+        ir.N = (int16_t)(mn >> 16);
+        ir.ta = (uint8_t)(w11 & 0xffu);
+        ir.tb = (uint8_t)((w11 >> 8) & 0xffu);
+        ir.flags = (uint8_t)((w11 >> 16) & 0xffu);
+        ir.kseg16 = (uint8_t)(w11 >> 24);
+        ireadc = ir.flags & kFlagReadC;
+        ikseg = 16 * (int)ir.kseg16;
         iseg = 0;
-        inseg = iK > 0 && ikseg > 0 ? (iK + ikseg - 1) / ikseg : 1;
-        const bool ok = iM >= 1 && iM <= kTwBlock && iN >= 1 && iN <= kTwBlock && iK >= 0 && ita <= 1 &&
-                        itb <= 1 && (iK == 0 || ikseg > 0) &&
-                        tw_ab_item_bytes(ita, itb, iM, iN, iK < ikseg ? iK : ikseg, true) <= RING / 2 &&
-                        tw_c_item_bytes(iM, iN) <= RING / 2;
+        inseg = ir.K > 0 && ikseg > 0 ? (ir.K + ikseg - 1) / ikseg : 1;
+        const bool ok = ir.M >= 1 && ir.M <= kTwBlockM && ir.N >= 1 && ir.N <= kTwBlockN && ir.K >= 0 &&
+                        ir.ta <= 1 && ir.tb <= 1 && (ir.K == 0 || ikseg > 0) && ir.lda > 0 && ir.ldb > 0 &&
+                        ir.ldc > 0 && tw_ab_item_bytes(ir, ir.K < ikseg ? ir.K : ikseg, true) <= RING / 2 &&
+                        tw_c_item_bytes(ir) <= RING / 2;
         if (!ok && lane == 0)
             set_error(p.err, kErrBadGroup);
         return ok;
@@ -443,11 +489,11 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         int k0 = 0, k1 = 0;
         uint32_t bytes;
         if (citem) {
-            bytes = tw_c_item_bytes(iM, iN);
+            bytes = tw_c_item_bytes(ir);
         } else {
             k0 = iseg * ikseg;
-            k1 = min(iK, k0 + ikseg);
-            bytes = tw_ab_item_bytes(ita, itb, iM, iN, k1 - k0, iseg == 0);
+            k1 = min(ir.K, k0 + ikseg);
+            bytes = tw_ab_item_bytes(ir, k1 - k0, iseg == 0);
         }
         uint32_t off = hoff, pad = 0;
         if (off + bytes > RING) {
@@ -462,7 +508,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         uint32_t fl = 0;
         if (citem) {
             fl = kTwCItem | kTwEpi;
-            tw_copy_runs(d, iC, 4 * (int64_t)ildc, iN, 4 * iM, lane);
+            tw_copy_op(d, ir.C, ir.ldc, ir.N, ir.M, (ir.flags & kTwSpanC) != 0, lane);
         } else {
             if (iseg == 0) {
                 fl |= kTwFirst;
@@ -472,15 +518,16 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
             }
             const int kl = k1 - k0;
             if (kl > 0) {
-                if (ita)
-                    tw_copy_runs(d, iA + 4 * (int64_t)k0, 4 * (int64_t)ilda, iM, 4 * kl, lane);
+                const bool sa = (ir.flags & kTwSpanA) != 0, sbb = (ir.flags & kTwSpanB) != 0;
+                if (ir.ta)
+                    tw_copy_op(d, ir.A + 4 * (int64_t)k0, ir.lda, ir.M, kl, sa, lane);
                 else
-                    tw_copy_runs(d, iA + 4 * (int64_t)k0 * ilda, 4 * (int64_t)ilda, kl, 4 * iM, lane);
-                d += tw_a_bytes(ita, iM, kl);
-                if (itb)
-                    tw_copy_runs(d, iB + 4 * (int64_t)k0 * ildb, 4 * (int64_t)ildb, kl, 4 * iN, lane);
+                    tw_copy_op(d, ir.A + 4 * (int64_t)k0 * ir.lda, ir.lda, kl, ir.M, sa, lane);
+                d += tw_a_bytes(ir.ta, ir.M, kl, ir.lda, sa);
+                if (ir.tb)
+                    tw_copy_op(d, ir.B + 4 * (int64_t)k0 * ir.ldb, ir.ldb, kl, ir.N, sbb, lane);
                 else
-                    tw_copy_runs(d, iB + 4 * (int64_t)k0, 4 * (int64_t)ildb, iN, 4 * kl, lane);
+                    tw_copy_op(d, ir.B + 4 * (int64_t)k0, ir.ldb, ir.N, kl, sbb, lane);
             }
             if (iseg == inseg - 1 && !ireadc)
                 fl |= kTwEpi;
@@ -548,15 +595,16 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
                 a.krun = cur.ta == 0;
                 b.krun = cur.tb != 0;
                 a.sec = sec;
-                b.sec = sec + tw_a_bytes(cur.ta, cur.M, kl);
-                a.D = (int)tw_run_slot(a.krun ? 4 * cur.M : 4 * kl);
-                b.D = (int)tw_run_slot(b.krun ? 4 * cur.N : 4 * kl);
+                const bool sa = (cur.flags & kTwSpanA) != 0, sbb = (cur.flags & kTwSpanB) != 0;
+                b.sec = sec + tw_a_bytes(cur.ta, cur.M, kl, cur.lda, sa);
+                a.D = sa ? 4 * cur.lda : (int)tw_run_slot(a.krun ? 4 * cur.M : 4 * kl);
+                b.D = sbb ? 4 * cur.ldb : (int)tw_run_slot(b.krun ? 4 * cur.N : 4 * kl);
                 a.b0 = (int)((reinterpret_cast<uintptr_t>(cur.A) +
                               (uintptr_t)(a.krun ? 4 * (int64_t)k0 * cur.lda : 4 * (int64_t)k0)) & 15u);
                 b.b0 = (int)((reinterpret_cast<uintptr_t>(cur.B) +
                               (uintptr_t)(b.krun ? 4 * (int64_t)k0 * cur.ldb : 4 * (int64_t)k0)) & 15u);
-                a.s16 = (4 * cur.lda) & 15;
-                b.s16 = (4 * cur.ldb) & 15;
+                a.s16 = sa ? 0 : (4 * cur.lda) & 15;
+                b.s16 = sbb ? 0 : (4 * cur.ldb) & 15;
                 const int nt = cur.N > 16 ? 32 : 16;
                 for (int kc = 0; kc < kl; kc += kTwKC) {
                     wait_mma();   // the A columns and the B tile are free once the last chunk's MMAs are done

@@ -32,33 +32,50 @@ struct TwParams {
     int32_t pad;
 };
 
-constexpr int kTwWarps = 12;      // warps per CTA (one CTA per SM), 32 accumulator columns of tensor memory each
+constexpr int kTwWarps = 12;      // warps per CTA (one CTA per SM)
 constexpr int kTwKC = 16;         // K values per converted operand chunk (one MMA K step of BF16 / FP16)
 constexpr int kTwMaxOut = 8;      // ring items in flight per warp
-constexpr int kTwBlock = 32;      // largest block side
+constexpr int kTwBlockM = 32;     // largest block height: one lane quarter of tensor memory
+constexpr int kTwBlockN = 32;     // largest block width: the warp's accumulator columns (16 or 32)
 constexpr int kTwThreads = 32 * kTwWarps;
 
-// Ring items.  A run is a contiguous stretch of one stored column (X bytes);
-// it is copied as the 16-byte granules that cover it into a slot of
-// tw_run_slot(X) bytes, its first element at the slot start plus the
-// address's offset within its granule (0, 4, 8 or 12).
-IAAT_HD uint32_t tw_run_slot(int xbytes) { return (uint32_t)((xbytes + 27) >> 4) << 4; }
-// op(A) rows r0.. (mh of them) x K range of kl values: runs along k (not
-// transposed: one per k) or along the rows (transposed: one per row)
-IAAT_HD uint32_t tw_a_bytes(int ta, int mh, int kl)
+// Ring items.  An operand block is R runs of len elements each (the
+// contiguous stretches of its stored columns, ld elements apart).  It is
+// staged either run by run -- each run as the 16-byte granules that cover it,
+// in a slot of tw_run_slot(4*len) bytes, its first element at the slot start
+// plus the address's offset within its granule (0, 4, 8 or 12) -- or, when
+// the ld padding between runs is small, as one span from its first element
+// to its last (the padding included): one run of 4*((R-1)*ld + len) bytes.
+IAAT_HD uint32_t tw_run_slot(int64_t xbytes) { return (uint32_t)((xbytes + 27) >> 4) << 4; }
+IAAT_HD uint32_t tw_op_bytes(int runs, int len, int64_t ld, bool span)
 {
-    return kl <= 0 ? 0u : (ta ? (uint32_t)mh * tw_run_slot(4 * kl) : (uint32_t)kl * tw_run_slot(4 * mh));
+    if (runs <= 0 || len <= 0)
+        return 0u;
+    return span ? tw_run_slot(4 * ((int64_t)(runs - 1) * ld + len)) : (uint32_t)runs * tw_run_slot(4 * (int64_t)len);
 }
-IAAT_HD uint32_t tw_b_bytes(int tb, int nw, int kl)
+// The block of op(A) (mh rows x a K range of kl values): runs along k when A
+// is not transposed (one per k, mh long), along the rows when it is; of
+// op(B) (kl x nw): one per column (kl long) when B is not transposed, one per
+// k (nw long) when it is; of C: one per column (mh long).
+IAAT_HD uint32_t tw_a_bytes(int ta, int mh, int kl, int64_t lda, bool span)
 {
-    return kl <= 0 ? 0u : (tb ? (uint32_t)kl * tw_run_slot(4 * nw) : (uint32_t)nw * tw_run_slot(4 * kl));
+    return ta ? tw_op_bytes(mh, kl, lda, span) : tw_op_bytes(kl, mh, lda, span);
 }
+IAAT_HD uint32_t tw_b_bytes(int tb, int nw, int kl, int64_t ldb, bool span)
+{
+    return tb ? tw_op_bytes(kl, nw, ldb, span) : tw_op_bytes(nw, kl, ldb, span);
+}
+IAAT_HD uint32_t tw_c_bytes(int mh, int nw, int64_t ldc, bool span) { return tw_op_bytes(nw, mh, ldc, span); }
+// Record flags beside kFlagReadC: which operands are staged as one span.
+constexpr uint8_t kTwSpanA = 2, kTwSpanB = 4, kTwSpanC = 8;
 // A task's items: its K range cut into kseg-value pieces (one item for K = 0),
-// the first one led by the task record; then, when C is read, one C item.
-IAAT_HD uint32_t tw_ab_item_bytes(int ta, int tb, int mh, int nw, int kl, bool first)
+// the first one led by the 64-byte task record; then, when C is read, one C
+// item.
+IAAT_HD uint32_t tw_ab_item_bytes(const TwTask &t, int kl, bool first)
 {
-    return (first ? 64u : 0u) + tw_a_bytes(ta, mh, kl) + tw_b_bytes(tb, nw, kl);
+    return (first ? 64u : 0u) + tw_a_bytes(t.ta, t.M, kl, t.lda, (t.flags & kTwSpanA) != 0) +
+           tw_b_bytes(t.tb, t.N, kl, t.ldb, (t.flags & kTwSpanB) != 0);
 }
-IAAT_HD uint32_t tw_c_item_bytes(int mh, int nw) { return (uint32_t)nw * tw_run_slot(4 * mh); }
+IAAT_HD uint32_t tw_c_item_bytes(const TwTask &t) { return tw_c_bytes(t.M, t.N, t.ldc, (t.flags & kTwSpanC) != 0); }
 
 }  // namespace iaat
