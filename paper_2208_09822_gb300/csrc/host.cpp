@@ -1330,7 +1330,7 @@ static double tw_task_cost(const TwTask &t)
     const int chunks = K > 0 ? (K + 15) / 16 : 0;
     const double bsteps = std::ceil((double)nw * 2 / 32.0);
     double c = 260.0 + chunks * (90.0 + 50.0 * bsteps + 120.0) + 8.0 * nw + 60.0;
-    const double slots = (K > 0 ? (double)tw_ab_item_bytes(t, K, false) : 0.0) +
+    const double slots = (K > 0 ? (double)tw_ab_item_bytes(t, K) : 0.0) +
                          ((t.flags & kFlagReadC) ? (double)tw_c_item_bytes(t) : 0.0);
     return c + 16.0 * std::ceil(slots / 16.0 / 32.0);
 }
@@ -1407,12 +1407,12 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
                             t.flags |= kTwSpanA;
                         if (g.transB ? tw_span(kl, nw, g.ldb) : tw_span(nw, kl, g.ldb))
                             t.flags |= kTwSpanB;
-                        while (kseg > 16 && tw_ab_item_bytes(t, std::min(K, kseg), true) > cap)
+                        while (kseg > 16 && tw_ab_item_bytes(t, std::min(K, kseg)) > cap)
                             kseg -= 16;
                     }
                 }
                 t.kseg16 = (uint8_t)(kseg / 16);
-                if (tw_ab_item_bytes(t, std::min(K, kseg), true) > cap || tw_c_item_bytes(t) > cap)
+                if (tw_ab_item_bytes(t, std::min(K, kseg)) > cap || tw_c_item_bytes(t) > cap)
                     return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: a block does not fit the staging ring",
                                 (long long)gi);
                 tasks.push_back(t);

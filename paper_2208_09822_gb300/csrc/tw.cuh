@@ -56,18 +56,31 @@ constexpr int kTwAccCols = kTwBlockN * kTwWarps;
 template <int P> IAAT_CE int tw_tmem_cols() { return kTwAccCols + (kTwWarps / 4) * TcTraits<P>::kTerms * tw_acols<P>(); }
 constexpr uint32_t kTwTmemAlloc = 512;
 // shared memory: the warps' mbarriers and the tensor-memory slot, then the
-// B tiles (one region per term), then the warps' rings
+// B tiles (one region per term), the warps' task-record rings, the warps'
+// staging rings
 constexpr int kTwCtl = 1024;
+constexpr int kTwRecSlots = 32;   // task records a warp holds (a power of two)
+constexpr int kTwRecAhead = 9;    // records are copied this many tasks ahead of their staging
 template <int P> IAAT_CE int tw_opB() { return kTwCtl; }
-template <int P> IAAT_CE int tw_ring_off() { return kTwCtl + TcTraits<P>::kTerms * tw_region<P>(); }
+template <int P> IAAT_CE int tw_rec_off() { return kTwCtl + TcTraits<P>::kTerms * tw_region<P>(); }
+template <int P> IAAT_CE int tw_ring_off() { return tw_rec_off<P>() + kTwWarps * kTwRecSlots * 64; }
 template <int P> IAAT_CE int tw_ring() { return ((kSmemTotal - tw_ring_off<P>()) / kTwWarps) & ~127; }
 static_assert(kTwWarps % 4 == 0 && kTwBlockM == 32 && (kTwBlockN == 16 || kTwBlockN == 32),
               "quads of warps, one lane quarter per block, MMA N of 16 or 32");
 static_assert(tw_tmem_cols<kTc6xBF16>() <= (int)kTwTmemAlloc && tw_tmem_cols<kTcTF32>() <= (int)kTwTmemAlloc,
               "tensor-memory columns");
 static_assert(kTwMaxOut == 8, "queue slots in lanes 0..7, cp.async groups");
+// The record of task t is copied in the cp.async group of task t - 9's first
+// item.  When task t is begun, at most kTwMaxOut items are in flight and the
+// first items of tasks t-8 .. t-1 came after that one, so the consumer has
+// already waited for its group; the slot is reused for task t + 32, copied
+// with task t + 23's first item, once the consumer is at least 16 items past
+// task t's first one.
+static_assert(kTwRecAhead > kTwMaxOut && kTwRecSlots >= kTwRecAhead + 2 * kTwMaxOut + 1 &&
+                  (kTwRecSlots & (kTwRecSlots - 1)) == 0,
+              "record ring");
 
-constexpr uint32_t kTwFirst = 1;   // the item starts with the task record
+constexpr uint32_t kTwFirst = 1;   // the task's first item
 constexpr uint32_t kTwCItem = 2;   // the item holds the staged C block
 constexpr uint32_t kTwEpi = 4;     // the block's epilogue follows this item
 
@@ -430,57 +443,57 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         it = p.wbeg[gw];
         te = p.wbeg[gw + 1];
     }
-    const uint32_t *words = reinterpret_cast<const uint32_t *>(p.tasks);
-    auto load_rec = [&](int t) -> uint32_t { return (lane < 16 && t < te) ? __ldg(words + (size_t)t * 16 + lane) : 0u; };
-    // issue side: the record of the task being staged (word l in lane l < 16)
-    // and the next three, prefetched
-    uint32_t rw = load_rec(it), r1 = load_rec(it + 1), r2 = load_rec(it + 2), r3 = load_rec(it + 3);
+    // the warp's record ring: task t's record in slot t mod kTwRecSlots
+    const char *recs = smem + tw_rec_off<P>() + warp * kTwRecSlots * 64;
+    const uint32_t recs_s = sb + (uint32_t)(tw_rec_off<P>() + warp * kTwRecSlots * 64);
+    auto fetch_rec = [&](int t) {
+        if (lane < 4 && t < te)
+            cp_async16(recs_s + (uint32_t)((t & (kTwRecSlots - 1)) * 64 + 16 * lane),
+                       reinterpret_cast<const char *>(p.tasks + t) + 16 * lane);
+    };
+    for (int r = 0; r < kTwRecAhead; ++r)
+        fetch_rec(it + r);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
     TwTask ir{};   // the task being staged
     int ireadc = 0, ikseg = 16, inseg = 1, iseg = 0;
-    // decode rw; false (and the error word set) for a record the kernel must refuse
+    // take task it's record; false (and the error word set) for a record the kernel must refuse
     auto begin = [&]() -> bool {
-        auto F = [&](int w) { return __shfl_sync(0xffffffffu, rw, w); };
-        ir.A = reinterpret_cast<const char *>(((uint64_t)F(1) << 32) | F(0));
-        ir.B = reinterpret_cast<const char *>(((uint64_t)F(3) << 32) | F(2));
-        ir.C = reinterpret_cast<char *>(((uint64_t)F(5) << 32) | F(4));
-        ir.lda = (int)F(6);
-        ir.ldb = (int)F(7);
-        ir.ldc = (int)F(8);
-        ir.K = (int)F(9);
-        const uint32_t mn = F(10), w11 = F(11);
-        ir.M = (int16_t)(mn & 0xffffu);
-        ir.N = (int16_t)(mn >> 16);
-        ir.ta = (uint8_t)(w11 & 0xffu);
-        ir.tb = (uint8_t)((w11 >> 8) & 0xffu);
-        ir.flags = (uint8_t)((w11 >> 16) & 0xffu);
-        ir.kseg16 = (uint8_t)(w11 >> 24);
+        ir = *reinterpret_cast<const TwTask *>(recs + (it & (kTwRecSlots - 1)) * 64);
         ireadc = ir.flags & kFlagReadC;
         ikseg = 16 * (int)ir.kseg16;
         iseg = 0;
         inseg = ir.K > 0 && ikseg > 0 ? (ir.K + ikseg - 1) / ikseg : 1;
         const bool ok = ir.M >= 1 && ir.M <= kTwBlockM && ir.N >= 1 && ir.N <= kTwBlockN && ir.K >= 0 &&
                         ir.ta <= 1 && ir.tb <= 1 && (ir.K == 0 || ikseg > 0) && ir.lda > 0 && ir.ldb > 0 &&
-                        ir.ldc > 0 && tw_ab_item_bytes(ir, ir.K < ikseg ? ir.K : ikseg, true) <= RING / 2 &&
+                        ir.ldc > 0 && tw_ab_item_bytes(ir, ir.K < ikseg ? ir.K : ikseg) <= RING / 2 &&
                         tw_c_item_bytes(ir) <= RING / 2;
         if (!ok && lane == 0)
             set_error(p.err, kErrBadGroup);
         return ok;
     };
-    auto next = [&]() {
-        ++it;
-        rw = r1;
-        r1 = r2;
-        r2 = r3;
-        r3 = load_rec(it + 3);
+    // move past refused records: their later records' copies are in no
+    // group the consumer waits for, so wait for every copy here (error path)
+    auto skip_refused = [&]() {
+        bool skipped = false;
+        while (it < te && !begin()) {
+            fetch_rec(it + kTwRecAhead);
+            ++it;
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            skipped = true;
+        }
+        return skipped;
     };
-    while (it < te && !begin())
-        next();
+    skip_refused();
 
     uint32_t head = 0, hoff = 0, tail = 0;   // ring: bytes allocated and freed (monotonic), offset of head
     int issued = 0, consumed = 0;
     // in-flight items: slot s (= item number mod kTwMaxOut) in lane s
     uint32_t q_off = 0, q_end = 0, q_fl = 0;
-    int q_k0 = 0, q_k1 = 0;
+    int q_k0 = 0, q_k1 = 0, q_t = 0;
     // Stage the next item of the current task if the ring has room for it.
     auto issue_one = [&]() -> bool {
         if (it >= te)
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         } else {
             k0 = iseg * ikseg;
             k1 = min(ir.K, k0 + ikseg);
-            bytes = tw_ab_item_bytes(ir, k1 - k0, iseg == 0);
+            bytes = tw_ab_item_bytes(ir, k1 - k0);
         }
         uint32_t off = hoff, pad = 0;
         if (off + bytes > RING) {
@@ -512,9 +525,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         } else {
             if (iseg == 0) {
                 fl |= kTwFirst;
-                if (lane < 4)
-                    cp_async16(d + 16u * (uint32_t)lane, reinterpret_cast<const char *>(p.tasks + it) + 16 * lane);
-                d += 64u;
+                fetch_rec(it + kTwRecAhead);
             }
             const int kl = k1 - k0;
             if (kl > 0) {
@@ -539,12 +550,12 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
             q_k0 = k0;
             q_k1 = k1;
             q_fl = fl;
+            q_t = it;
         }
         ++issued;
         if (++iseg == inseg + ireadc) {
-            next();
-            while (it < te && !begin())
-                next();
+            ++it;
+            skip_refused();
         }
         return true;
     };
@@ -573,6 +584,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         const uint32_t off = __shfl_sync(0xffffffffu, q_off, s), end = __shfl_sync(0xffffffffu, q_end, s);
         const uint32_t fl = __shfl_sync(0xffffffffu, q_fl, s);
         const int k0 = __shfl_sync(0xffffffffu, q_k0, s), k1 = __shfl_sync(0xffffffffu, q_k1, s);
+        const int ct = __shfl_sync(0xffffffffu, q_t, s);
         cp_async_wait_upto(issued - consumed - 1);
         __syncwarp();
         const char *item = ring + off;
@@ -585,10 +597,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
             tc_fence_before();
         } else {
             const char *sec = item;
-            if (fl & kTwFirst) {
-                cur = tw_read_record(item);
-                sec += 64;
-            }
+            if (fl & kTwFirst)
+                cur = tw_read_record(recs + (ct & (kTwRecSlots - 1)) * 64);
             const int kl = k1 - k0;
             if (kl > 0) {
                 TwSide a, b;

@@ -68,12 +68,11 @@ IAAT_HD uint32_t tw_b_bytes(int tb, int nw, int kl, int64_t ldb, bool span)
 IAAT_HD uint32_t tw_c_bytes(int mh, int nw, int64_t ldc, bool span) { return tw_op_bytes(nw, mh, ldc, span); }
 // Record flags beside kFlagReadC: which operands are staged as one span.
 constexpr uint8_t kTwSpanA = 2, kTwSpanB = 4, kTwSpanC = 8;
-// A task's items: its K range cut into kseg-value pieces (one item for K = 0),
-// the first one led by the 64-byte task record; then, when C is read, one C
-// item.
-IAAT_HD uint32_t tw_ab_item_bytes(const TwTask &t, int kl, bool first)
+// A task's items: its K range cut into kseg-value pieces (one empty item for
+// K = 0); then, when C is read, one C item.
+IAAT_HD uint32_t tw_ab_item_bytes(const TwTask &t, int kl)
 {
-    return (first ? 64u : 0u) + tw_a_bytes(t.ta, t.M, kl, t.lda, (t.flags & kTwSpanA) != 0) +
+    return tw_a_bytes(t.ta, t.M, kl, t.lda, (t.flags & kTwSpanA) != 0) +
            tw_b_bytes(t.tb, t.N, kl, t.ldb, (t.flags & kTwSpanB) != 0);
 }
 IAAT_HD uint32_t tw_c_item_bytes(const TwTask &t) { return tw_c_bytes(t.M, t.N, t.ldc, (t.flags & kTwSpanC) != 0); }
