@@ -209,17 +209,10 @@ __device__ __forceinline__ void tw_convert_a(const TwSide &s, int M, int kc, int
     float x[kTwKC];
     const int row = lane < M ? lane : 0;
     const char *p = s.krun ? s.sec + kc * s.D + 4 * row : s.sec + row * s.D + ((s.b0 + row * s.s16) & 15) + 4 * kc;
-    if (kc + kTwKC <= kl) {
 #pragma unroll
-        for (int v = 0; v < kTwKC; ++v)
-            x[v] = *reinterpret_cast<const float *>(p + (s.krun ? v * s.D + ((s.b0 + v * s.s16) & 15) : 4 * v));
-    } else {
-#pragma unroll
-        for (int v = 0; v < kTwKC; ++v)
-            x[v] = kc + v < kl
-                       ? *reinterpret_cast<const float *>(p + (s.krun ? v * s.D + ((s.b0 + v * s.s16) & 15) : 4 * v))
-                       : 0.0f;
-    }
+    for (int v = 0; v < kTwKC; ++v)
+        x[v] = kc + v < kl ? *reinterpret_cast<const float *>(p + (s.krun ? v * s.D + ((s.b0 + v * s.s16) & 15) : 4 * v))
+                           : 0.0f;
     if constexpr (P == kTcTF32) {
         uint32_t w[16];
 #pragma unroll
@@ -271,21 +264,14 @@ __device__ __forceinline__ void tw_convert_b(const TwSide &s, int rows, int kc, 
     for (int v = 0; v < V; ++v)
         o[v] = s.krun ? v * s.D + ((s.b0 + v * s.s16) & 15) : 4 * v;
     const int n = rows * G;
-#pragma unroll 2
     for (int e = lane; e < n; e += 32) {
         const int row = e >> LG, g = e & (G - 1);
         const int k = kc + g * V;   // first k of this core row
         const char *p = s.krun ? s.sec + k * s.D + 4 * row : s.sec + row * s.D + ((s.b0 + row * s.s16) & 15) + 4 * k;
         float x[8];
-        if (k + V <= kl) {
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                x[v] = *reinterpret_cast<const float *>(p + o[v]);
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                x[v] = k + v < kl ? *reinterpret_cast<const float *>(p + o[v]) : 0.0f;
-        }
+        for (int v = 0; v < V; ++v)
+            x[v] = k + v < kl ? *reinterpret_cast<const float *>(p + o[v]) : 0.0f;
         store_row<P>(t0, t1, t2, (uint32_t)((row >> 3) * SBO + (row & 7) * 16 + g * 128), x);
     }
 }
@@ -366,44 +352,32 @@ __device__ __forceinline__ void tw_epilogue(const TwCur &t, const char *citem, u
         return;
     float *cp = t.C + lane;
     const int64_t ldc = t.ldc;
-    if (t.readc) {
-        const bool span = (t.flags & kTwSpanC) != 0;
-        const int DC = span ? (int)(4 * ldc) : (int)tw_run_slot(4 * t.M);
-        const int c0 = (int)(reinterpret_cast<uintptr_t>(t.C) & 15u), s16 = span ? 0 : (int)((4 * ldc) & 15);
-        int mis[4];
+    // C0 is read only when beta != 0 (it may hold anything otherwise)
+    const bool span = (t.flags & kTwSpanC) != 0;
+    const int DC = span ? (int)(4 * ldc) : (int)tw_run_slot(4 * t.M);
+    const int c0 = (int)(reinterpret_cast<uintptr_t>(t.C) & 15u), s16 = span ? 0 : (int)((4 * ldc) & 15);
+    int mis[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            mis[u] = (c0 + u * s16) & 15;
-        const char *sp = citem + 4 * lane;
-        // eight columns at a time: their C0 loads issue together
+    for (int u = 0; u < 4; ++u)
+        mis[u] = (c0 + u * s16) & 15;
+    const char *sp = citem + 4 * lane;
+    const float beta = t.readc ? t.beta : 0.0f;
+    // eight columns at a time: their C0 loads issue together
 #pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += 8) {
-            if (j0 >= t.N)
-                break;
-            float c[8];
+    for (int j0 = 0; j0 < 32; j0 += 8) {
+        if (j0 >= t.N)
+            break;
+        float c[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                c[u] = j0 + u < t.N ? *reinterpret_cast<const float *>(sp + u * DC + mis[u & 3]) : 0.0f;
+        for (int u = 0; u < 8; ++u)
+            c[u] = t.readc && j0 + u < t.N ? *reinterpret_cast<const float *>(sp + u * DC + mis[u & 3]) : 0.0f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (j0 + u < t.N)
-                    __stcs(cp, fmaf(t.beta, c[u], t.alpha * __uint_as_float(acc[j0 + u])));
-                cp += ldc;
-            }
-            sp += 8 * DC;
+        for (int u = 0; u < 8; ++u) {
+            if (j0 + u < t.N)
+                __stcs(cp, fmaf(beta, c[u], t.alpha * __uint_as_float(acc[j0 + u])));
+            cp += ldc;
         }
-    } else {
-#pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += 8) {
-            if (j0 >= t.N)
-                break;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (j0 + u < t.N)
-                    __stcs(cp, t.alpha * __uint_as_float(acc[j0 + u]));
-                cp += ldc;
-            }
-        }
+        sp += 8 * DC;
     }
 }
 
@@ -517,31 +491,35 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
             return false;
         head += pad + bytes;
         hoff = off + bytes;
-        uint32_t d = ring_s + off;
         uint32_t fl = 0;
+        // the item's operand blocks (C; or op(A) then op(B)), one copy call site
+        const int kl = k1 - k0;
         if (citem) {
             fl = kTwCItem | kTwEpi;
-            tw_copy_op(d, ir.C, ir.ldc, ir.N, ir.M, (ir.flags & kTwSpanC) != 0, lane);
         } else {
             if (iseg == 0) {
                 fl |= kTwFirst;
                 fetch_rec(it + kTwRecAhead);
             }
-            const int kl = k1 - k0;
-            if (kl > 0) {
-                const bool sa = (ir.flags & kTwSpanA) != 0, sbb = (ir.flags & kTwSpanB) != 0;
-                if (ir.ta)
-                    tw_copy_op(d, ir.A + 4 * (int64_t)k0, ir.lda, ir.M, kl, sa, lane);
-                else
-                    tw_copy_op(d, ir.A + 4 * (int64_t)k0 * ir.lda, ir.lda, kl, ir.M, sa, lane);
-                d += tw_a_bytes(ir.ta, ir.M, kl, ir.lda, sa);
-                if (ir.tb)
-                    tw_copy_op(d, ir.B + 4 * (int64_t)k0 * ir.ldb, ir.ldb, kl, ir.N, sbb, lane);
-                else
-                    tw_copy_op(d, ir.B + 4 * (int64_t)k0, ir.ldb, ir.N, kl, sbb, lane);
-            }
             if (iseg == inseg - 1 && !ireadc)
                 fl |= kTwEpi;
+        }
+        uint32_t d = ring_s + off;
+        const int nops = citem ? 1 : (kl > 0 ? 2 : 0);
+        for (int o = 0; o < nops; ++o) {
+            const bool isb = o == 1;
+            const int tr = citem ? 0 : (isb ? ir.tb : ir.ta);
+            const int64_t ld = citem ? ir.ldc : (isb ? ir.ldb : ir.lda);
+            const int rows = citem || !isb ? ir.M : ir.N;   // block rows of C / op(A), columns of op(B)
+            const bool span = (ir.flags & (citem ? kTwSpanC : (isb ? kTwSpanB : kTwSpanA))) != 0;
+            // runs along k: op(A) not transposed, op(B) transposed; else one run per row / column
+            const bool krun = !citem && (isb ? tr != 0 : tr == 0);
+            const char *base = citem ? ir.C : (isb ? ir.B : ir.A);
+            const char *src = citem ? base : base + 4 * (krun ? (int64_t)k0 * ld : (int64_t)k0);
+            const int R = citem ? ir.N : (krun ? kl : rows);
+            const int len = citem ? ir.M : (krun ? rows : kl);
+            tw_copy_op(d, src, ld, R, len, span, lane);
+            d += tw_op_bytes(R, len, ld, span);
         }
         cp_async_commit();
         if (lane == (issued & (kTwMaxOut - 1))) {
@@ -588,14 +566,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         cp_async_wait_upto(issued - consumed - 1);
         __syncwarp();
         const char *item = ring + off;
-        if (fl & kTwCItem) {
-            wait_mma();
-            if (abort)
-                break;
-            tc_fence_after();
-            tw_epilogue(cur, item, dcol + lq, cur.K > 0, cur.N > 16 ? 32 : 16, lane);
-            tc_fence_before();
-        } else {
+        if (!(fl & kTwCItem)) {
             const char *sec = item;
             if (fl & kTwFirst)
                 cur = tw_read_record(recs + (ct & (kTwRecSlots - 1)) * 64);
@@ -638,14 +609,15 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
                 if (abort)
                     break;
             }
-            if (fl & kTwEpi) {
-                wait_mma();
-                if (abort)
-                    break;
-                tc_fence_after();
-                tw_epilogue(cur, nullptr, dcol + lq, cur.K > 0, cur.N > 16 ? 32 : 16, lane);
-                tc_fence_before();
-            }
+        }
+        // the block's epilogue: after its C item, or after its last item when C is not read
+        if (fl & kTwEpi) {
+            wait_mma();
+            if (abort)
+                break;
+            tc_fence_after();
+            tw_epilogue(cur, item, dcol + lq, cur.K > 0, cur.N > 16 ? 32 : 16, lane);
+            tc_fence_before();
         }
         __syncwarp();
         tail = end;
