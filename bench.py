@@ -116,25 +116,26 @@ KERNEL_UNITS = {"ffma": "kernels_fma.cu", "dfma": "kernels_fma.cu", "cgemm": "ke
                 "zgemm": "kernels_cplx.cu"}
 
 
-def kernel_unit(precision):
+def kernel_unit(precision, family=None):
+    """The translation unit of a path's kernel; `family` is the plan's
+    kernel_family (1 stage, 2 stream, 3 warp-tile), else the path's suffix."""
     base = ROUTE_BASE(precision)
-    stream = precision.endswith("@stream")
-    if precision.endswith("@warp"):
-        return "kernels_tw.cu"
+    if family is None:
+        family = KERNEL.get(precision, 0) or 1
     if base in ("ffma", "dfma"):
-        return "kernels_ws.cu" if stream else KERNEL_UNITS[base]
+        return "kernels_ws.cu" if family == 2 else KERNEL_UNITS[base]
     if base in KERNEL_UNITS:
         return KERNEL_UNITS[base]
-    return "kernels_tc2.cu" if stream else "kernels_tc.cu"
+    return {2: "kernels_tc2.cu", 3: "kernels_tw.cu"}.get(family, "kernels_tc.cu")
 
 
-def kernel_source_hash(precision="3xbf16"):
+def kernel_source_hash(precision="3xbf16", family=None):
     """Hash of the sources a path's kernel is compiled from: its translation
     unit and every header it includes (launch.h, which only declares the
     host launchers, aside), so a profile stays current while that kernel's
     code is unchanged."""
     csrc = os.path.join(ROOT, "paper_2208_09822_gb300", "csrc")
-    seen, todo = set(), [kernel_unit(precision)]
+    seen, todo = set(), [kernel_unit(precision, family)]
     while todo:
         f = todo.pop()
         if f in seen or f == "launch.h" or not os.path.exists(os.path.join(csrc, f)):
@@ -149,7 +150,7 @@ def kernel_source_hash(precision="3xbf16"):
     return h.hexdigest()[:16]
 
 
-def profile_traffic(precision, workload="uneven", count=200_000):
+def profile_traffic(precision, workload="uneven", count=200_000, family=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"grouped_{precision}_{workload}{count // 1000}k.md")
@@ -162,7 +163,7 @@ def profile_traffic(precision, workload="uneven", count=200_000):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_hash") != kernel_source_hash(precision):
+    if kv.get("kernel_source_hash") != kernel_source_hash(precision, family):
         return None
     try:
         return float(kv["dram_bytes_per_launch_full"])
@@ -723,7 +724,9 @@ def main():
         cpu, errs = None, {}
         if world == 1 and not args.no_cpu_baseline:
             cpu, errs = cpu_baseline_leg(batch, {k: v[2] for k, v in results.items()}, 10.0, wl_tol)
-        traffic = profile_traffic(args.precision, args.workload, batch.count)
+        # a profile counts only for the kernel family this plan runs (the
+        # autotuner may pick another one for a default path)
+        traffic = profile_traffic(args.precision, args.workload, batch.count, info.get("kernel_family"))
         paths = {}
         for name, (inf, ms_p, _) in results.items():
             paths[name] = {"value": job_flops / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s",
@@ -757,7 +760,9 @@ def main():
                              if rot == 1 else ("pools %.0f MB fit L2: launches rotate over %d copies (%.0f MB); "
                                                "no flush" % (pool_bytes / 1e6, rot, rot * pool_bytes / 1e6)),
                        "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
-                       "grid": info["grid"], "tuning": tuned},
+                       "grid": info["grid"], "tuning": tuned,
+                       "kernel_family": {1: "stage programs", 2: "stream", 3: "warp-tile"}.get(
+                           info.get("kernel_family"), "unknown")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value if e2e_ok else None, "unit": "GFLOP/s", "ok": e2e_ok,

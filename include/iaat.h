@@ -163,6 +163,10 @@ typedef struct {
     int32_t kernels;           /* kernels one iaat_gemm_grouped launches (2 when a
                                   tensor-core plan routes small-K instances) */
     int32_t dtype, precision;
+    int32_t kernel_family;     /* the kernels the plan runs: 1 stage programs, 2 stream
+                                  (warp-stream / pack-stream), 3 warp-tile; for a routed
+                                  plan, its tensor-core part's */
+    int32_t reserved;
 } iaat_plan_info_t;
 
 /* Single small GEMM, FP32 / FP64 (BLAS sgemm/dgemm argument order, Sec. I).

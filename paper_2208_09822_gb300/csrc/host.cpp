@@ -934,6 +934,7 @@ static iaat_status_t plan_create_ws(const iaat_gemm_desc_t *descs, int64_t count
     info.plan_bytes = (int64_t)(tb + wb + 256);
     info.grid = grid;
     info.kernels = nt > 0 ? 1 : 0;
+    info.kernel_family = 2;
     plan->info = info;
     *out = plan;
     return IAAT_OK;
@@ -1303,6 +1304,7 @@ static iaat_status_t plan_create_tc2(const iaat_gemm_desc_t *descs, int64_t coun
     info.plan_bytes = (int64_t)(pb + ob + gb + sizeof(int32_t));
     info.grid = grid;
     info.kernels = npacks > 0 ? 1 : 0;
+    info.kernel_family = 2;
     plan->info = info;
     *out = plan;
     return IAAT_OK;
@@ -1503,6 +1505,7 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
     info.plan_bytes = (int64_t)(tb + wb + 256);
     info.grid = grid;
     info.kernels = nt > 0 ? 1 : 0;
+    info.kernel_family = 3;
     plan->info = info;
     *out = plan;
     return IAAT_OK;
@@ -1541,9 +1544,11 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
             ctas_per_sm = 1;   // the kernel takes all shared memory: one CTA per SM
     }
     (void)ctas_per_sm;
-    const int kernel = opts ? opts->kernel : 0;
+    int kernel = opts ? opts->kernel : 0;
     if (kernel < 0 || kernel > 3)
         return fail(IAAT_ERR_INVALID_VALUE, "kernel %d out of range", kernel);
+    if (kernel == 0 && dt == IAAT_F32)
+        kernel = tuning().kernel[(int)precision];   // the autotuner's choice (0: stage programs)
     if (kernel == 3 && !tc)
         return fail(IAAT_ERR_INVALID_VALUE, "kernel 3 (warp-tile tensor-core kernel) needs a tensor-core precision");
     if (tc && kernel == 3)
@@ -1673,6 +1678,7 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     info.plan_bytes = (int64_t)(pb + ob + sizeof(int32_t) + scal_bytes);
     info.grid = plan->grid;
     info.kernels = plan->ngroups > 0 ? 1 : 0;
+    info.kernel_family = 1;
     plan->info = info;
     *out = plan;
     return IAAT_OK;

@@ -7,7 +7,11 @@
 //    time to the tiler's cost model becomes the variant's cost scale, so the
 //    run-time tiler (Sec. V-A) ranks variants by what they really cost here;
 //  * for every kernel, the stage size (tasks per pipeline stage) on an
-//    uneven batch shaped like the workload the library targets.
+//    uneven batch shaped like the workload the library targets;
+//  * for FP32, on the same batch, which kernel family a default plan runs:
+//    the stage-program kernels, the stream kernels, or (tensor-core
+//    precisions) the warp-tile kernel; another family than the stage
+//    programs only when it is at least 3 % faster.
 // The result is written as JSON and read back by later processes through
 // IAAT_TUNE_CACHE (or applied to the calling process at once).
 #include <cuda_runtime.h>
@@ -83,6 +87,10 @@ void apply_text(const std::string &txt, Tuning &t)
             a = true;
     }
     read_int(txt, "group_tasks_dfma", &t.group_tasks_f64, 1, kMaxGroupTasks);
+    for (int i = 0; i < 5; ++i) {
+        static const char *keys[5] = {"kernel_ffma", "kernel_3xbf16", "kernel_tf32", "kernel_fp16", "kernel_6xbf16"};
+        read_int(txt, keys[i], &t.kernel[i], 1, i == 0 ? 2 : 3);
+    }
     t.from_cache = a || b;
 }
 
@@ -328,6 +336,7 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
                 break;
             iaat_plan_options_t o{};
             o.force_variant = v + 1;
+            o.kernel = 1;   // the stage-program kernel, whose tiler the scales serve
             double ms = 0;
             st = time_plan(b, dtype, precision, o, s, &ms);
             ratio[v] = ms / model;
@@ -348,7 +357,7 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
         }
     }
     // stage size on an uneven batch
-    int best_group = 0;
+    int best_group = 0, best_kernel = 0;
     if (st == IAAT_OK) {
         std::vector<int> shapes;
         const int count = 60000;
@@ -375,11 +384,27 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
                 break;
             iaat_plan_options_t o{};
             o.max_group_tasks = gt;
+            o.kernel = 1;
             double ms = 0;
             st = time_plan(b, dtype, precision, o, s, &ms);
             if (st == IAAT_OK && ms < best) {
                 best = ms;
                 best_group = gt;
+            }
+        }
+        // the kernel family of the default FP32 plans
+        if (st == IAAT_OK && dtype == IAAT_F32) {
+            best_kernel = 1;
+            const double stage = best;
+            for (int k = 2; k <= (precision == IAAT_PREC_DEFAULT ? 2 : 3) && st == IAAT_OK; ++k) {
+                iaat_plan_options_t o{};
+                o.kernel = k;
+                double ms = 0;
+                st = time_plan(b, dtype, precision, o, s, &ms);
+                if (st == IAAT_OK && ms < 0.97 * stage && ms < best) {
+                    best = ms;
+                    best_kernel = k;
+                }
             }
         }
     }
@@ -390,6 +415,8 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
         t.group_tasks_f64 = best_group;
     else
         t.group_tasks[(int)precision] = best_group;
+    if (dtype == IAAT_F32)
+        t.kernel[(int)precision] = best_kernel;
     t.from_cache = true;
     {
         std::lock_guard<std::mutex> lk(g_mutex);
@@ -417,7 +444,10 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
                      t.group_tasks[1]);
         std::fprintf(f, "  \"group_tasks_tf32\": %d,\n  \"group_tasks_fp16\": %d,\n  \"group_tasks_6xbf16\": %d,\n",
                      t.group_tasks[2], t.group_tasks[3], t.group_tasks[4]);
-        std::fprintf(f, "  \"group_tasks_dfma\": %d\n}\n", t.group_tasks_f64);
+        std::fprintf(f, "  \"group_tasks_dfma\": %d,\n", t.group_tasks_f64);
+        std::fprintf(f, "  \"kernel_ffma\": %d,\n  \"kernel_3xbf16\": %d,\n  \"kernel_tf32\": %d,\n", t.kernel[0],
+                     t.kernel[1], t.kernel[2]);
+        std::fprintf(f, "  \"kernel_fp16\": %d,\n  \"kernel_6xbf16\": %d\n}\n", t.kernel[3], t.kernel[4]);
         std::fclose(f);
     }
     return IAAT_OK;

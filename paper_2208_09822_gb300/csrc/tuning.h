@@ -15,6 +15,10 @@ struct Tuning {
     float scale_f64[kNumVariantsF64];
     int group_tasks[5] = {0, 0, 0, 0, 0};   // tasks per stage, by iaat_precision_t (0: default)
     int group_tasks_f64 = 0;             // same for FP64 (0: kMaxGroupTasks)
+    // the kernel family a default FP32 plan (option kernel = 0) runs, by
+    // iaat_precision_t: 1 stage programs, 2 stream, 3 warp-tile (tensor-core
+    // precisions only); 0: not tuned (stage programs)
+    int kernel[5] = {0, 0, 0, 0, 0};
     bool from_cache = false;
     Tuning()
     {

@@ -55,7 +55,7 @@ class PlanInfo(ctypes.Structure):
                 ("groups", ctypes.c_int64), ("blocks", ctypes.c_int64), ("flops", ctypes.c_int64),
                 ("algorithmic_bytes", ctypes.c_int64), ("plan_bytes", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("kernels", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("kernel_family", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None

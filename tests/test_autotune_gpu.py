@@ -1,6 +1,7 @@
 """The autotuner (the GPU counterpart of the paper's install-time tuning):
-it times the register-tile variants and the stage size on this GPU, writes a
-JSON cache, and plans made with the tuned model stay correct."""
+it times the register-tile variants, the stage size and the kernel family of
+default FP32 plans on this GPU, writes a JSON cache, and plans made with the
+tuned model stay correct."""
 import json
 import os
 import subprocess
@@ -31,11 +32,16 @@ def test_autotune_writes_cache_and_tuned_plans_stay_correct(tmp_path):
     path = str(tmp_path / "tune.json")
     iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, path)
     iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, path)
+    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_FP16, path)
     cache = json.load(open(path))
     assert len(cache["variant_scale_f32"]) == 5
     assert all(v > 0 for v in cache["variant_scale_f32"])
     assert cache["group_tasks_ffma"] in (8, 16, 24, 32)
     assert cache["group_tasks_3xbf16"] in (8, 16, 24, 32)
+    # the kernel family each default plan runs: stage programs or stream for
+    # FP32 on the CUDA cores, any of the three for the tensor-core paths
+    assert cache["kernel_ffma"] in (1, 2)
+    assert cache["kernel_3xbf16"] in (1, 2, 3) and cache["kernel_fp16"] in (1, 2, 3)
     # a fresh process reads the cache through IAAT_TUNE_CACHE and still
     # matches the oracle
     code = (
@@ -45,11 +51,13 @@ def test_autotune_writes_cache_and_tuned_plans_stay_correct(tmp_path):
         "b = W.random_small(1500, seed=91, max_dim=60, pad_max=3)\n"
         "import numpy as np\n"
         "b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])\n"
-        "for prec in (0, 1):\n"
-        "    C, _ = run_grouped(b, prec)\n"
+        "fam = %r\n"
+        "for prec, tol in ((0, 1e-5), (1, 1e-5), (3, 1e-3)):\n"
+        "    C, info = run_grouped(b, prec)\n"
+        "    assert info['kernel_family'] == fam[prec], (prec, info)\n"
         "    e = compare(b, C)\n"
-        "    assert e['eps_batch'] <= 1e-5, e\n"
-        "print('ok')\n" % (ROOT, ROOT))
+        "    assert e['eps_batch'] <= tol, e\n"
+        "print('ok')\n" % (ROOT, ROOT, {0: cache["kernel_ffma"], 1: cache["kernel_3xbf16"], 3: cache["kernel_fp16"]}))
     env = dict(os.environ, IAAT_TUNE_CACHE=path)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
@@ -65,7 +73,7 @@ def test_cache_applies_only_on_the_gpu_it_was_measured_on(tmp_path):
     cache = json.load(open(path))
     for key in ("device", "sm_count", "compute_capability", "driver_version", "runtime_version"):
         assert key in cache, key
-    forced = dict(cache, group_tasks_ffma=8)
+    forced = dict(cache, group_tasks_ffma=8, kernel_ffma=1)
     other = dict(forced, device=cache["device"] + " (another GPU)")
     paths = {}
     for name, c in (("forced", forced), ("other", other)):
