@@ -384,7 +384,7 @@ def run_sweep(args):
         for n in (1, 2, 4, 8, 16, 32, 48, 64, 80):
             if not W.in_domain(n, n, n, *W.TRANS_CASES[case]):
                 continue
-            for dtype, paths in ((np.float32, ("ffma", "3xbf16")), (np.float64, ("dfma",))):
+            for dtype, paths in ((np.float32, tuple(args.sweep_paths)), (np.float64, ("dfma",))):
                 b = W.sweep(case, (n, n, n), dtype=dtype, count=4096)
                 tA = torch.from_numpy(b.A).to(dev)
                 tB = torch.from_numpy(b.B).to(dev)
@@ -392,7 +392,7 @@ def run_sweep(args):
                 descs = iaat.descs_for_pools(b, tA.data_ptr(), tB.data_ptr(), tC.data_ptr())
                 for path in paths:
                     plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32 if dtype == np.float32 else iaat.IAAT_F64,
-                                                 iaat.IAAT_PREC_3XBF16 if path == "3xbf16" else 0)
+                                                 PRECISIONS.get(path, 0), kernel=KERNEL.get(path, 0))
                     info = iaat.iaat_plan_info(plan)
                     with torch.cuda.stream(stream):
                         for _ in range(3):
@@ -409,13 +409,13 @@ def run_sweep(args):
                     iaat.iaat_plan_check(plan, stream)
                     ms = e0.elapsed_time(e1) / reps
                     launches += reps + 3
-                    t_roof = max(info["algorithmic_bytes"] / (peaks["hbm_gbs"] * 1e9),
-                                 info["flops"] / (pipe[path] * 1e9))
+                    pk = pipe[ROUTE_BASE(path) if ROUTE_BASE(path) in pipe else "3xbf16"]
+                    t_roof = max(info["algorithmic_bytes"] / (peaks["hbm_gbs"] * 1e9), info["flops"] / (pk * 1e9))
                     rows.append({"case": case, "n": n, "path": path, "us": ms * 1e3,
                                  "gflops": info["flops"] / (ms * 1e-3) / 1e9,
                                  "roofline_frac": t_roof / (ms * 1e-3),
                                  "bound": "hbm" if info["algorithmic_bytes"] / (peaks["hbm_gbs"] * 1e9)
-                                 >= info["flops"] / (pipe[path] * 1e9) else path})
+                                 >= info["flops"] / (pk * 1e9) else path})
                     plan.destroy()
                 del tA, tB, tC
     print(json.dumps({"metric": "same-size sweep GFLOP/s and roofline fraction (M = N = K)", "unit": "GFLOP/s",
@@ -452,6 +452,8 @@ def main():
                     help="instances of the batch (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--sweep", action="store_true",
                     help="time same-size batches on the M = N = K diagonal (prints its own JSON line)")
+    ap.add_argument("--sweep-paths", default="ffma,3xbf16", type=lambda v: [x for x in v.split(",") if x],
+                    help="FP32 paths of --sweep (name, name@stage, name@stream, name@warp)")
     ap.add_argument("--pack-ablation", action="store_true",
                     help="time the pack step against the no-pack path by size (prints its own JSON line)")
     ap.add_argument("--split", default="replicate", choices=["replicate", "shard"],

@@ -242,7 +242,14 @@ iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t c
  * persistent schedule and copies the descriptors to the device (synchronous;
  * uses the current CUDA device).  The plan keeps the pointers: re-plan when
  * they change.  `opts` may be NULL.  dtype IAAT_F32 or IAAT_F64 (complex
- * dtypes: iaat_plan_create_complex; here IAAT_ERR_INVALID_VALUE). */
+ * dtypes: iaat_plan_create_complex; here IAAT_ERR_INVALID_VALUE).
+ * A default tensor-core plan (opts NULL or kernel 0, on the stage programs)
+ * sends the instances a pipeline stage cannot hold whole to the warp-tile
+ * kernel, which stages K in pieces; one iaat_gemm_grouped then launches both
+ * (iaat_plan_info: kernels).  On the stage programs alone (kernel 1) such
+ * instances are cut into row / column pieces, and one whose row of A and
+ * column of B do not fit a stage (e.g. 1 x 1 x 20000) is rejected with
+ * IAAT_ERR_UNSUPPORTED. */
 iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t count,
                                iaat_dtype_t dtype, iaat_precision_t precision,
                                const iaat_plan_options_t *opts,

@@ -1512,9 +1512,38 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
 }
 
 
+// Options that pin the stage programs' tiling or stages (a forced variant
+// or stage size, an injected fault) keep a plan on the stage programs alone.
+static bool opts_force_free(const iaat_plan_options_t *o)
+{
+    return !o || (o->force_variant <= 0 && o->max_group_tasks <= 0 && o->inject_fault == 0);
+}
+
+// Append plan b after the last plan of a's chain (one iaat_gemm_grouped
+// launches them in order) and add b's statistics to a's.
+static void chain_plan(iaat_plan_t a, iaat_plan_t b)
+{
+    iaat_plan_t last = a;
+    while (last->sub)
+        last = last->sub;
+    last->sub = b;
+    iaat_plan_info_t &x = a->info;
+    const iaat_plan_info_t &y = b->info;
+    x.active += y.active;
+    x.tasks += y.tasks;
+    x.groups += y.groups;
+    x.blocks += y.blocks;
+    x.flops += y.flops;
+    x.algorithmic_bytes += y.algorithmic_bytes;
+    x.plan_bytes += y.plan_bytes;
+    x.grid = std::max(x.grid, y.grid);
+    x.kernels += y.kernels;
+}
+
 static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t count, int dt,
                                       iaat_precision_t precision, const iaat_plan_options_t *opts,
-                                      const double *cscal, iaat_plan_t *out, const int64_t *index_map = nullptr)
+                                      const double *cscal, iaat_plan_t *out, const int64_t *index_map = nullptr,
+                                      bool split_large = true)
 {
     const int esz = dtype_esz(dt);
     const bool tc = precision != IAAT_PREC_DEFAULT;
@@ -1557,6 +1586,51 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
         return plan_create_ws(descs, count, opts, force_variant, out, index_map);
     if (tc && kernel == 2)
         return plan_create_tc2(descs, count, precision, opts, out, index_map);
+
+    // A default tensor-core plan on the stage programs sends the instances
+    // that a stage cannot hold whole -- the ones the stage programs would cut
+    // into row / column pieces, each re-reading the shared operand -- to the
+    // warp-tile kernel, which stages K in pieces instead (64^3 same-size
+    // batches 2.6x faster there); that plan runs after this one on the same
+    // stream.
+    if (tc && split_large && (!opts || opts->kernel == 0) && opts_force_free(opts)) {
+        std::vector<iaat_gemm_desc_t> dst, dlg;
+        std::vector<int64_t> ist, ilg;
+        for (int64_t i = 0; i < count; ++i) {
+            const iaat_gemm_desc_t &g = descs[i];
+            const int64_t gi = index_map ? index_map[i] : i;
+            const iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A,
+                                                    g.B, g.C, g.alpha, 4);
+            if (st != IAAT_OK)
+                return st;
+            const int Keff = g.alpha == 0.0 ? 0 : g.K;
+            int pm = 1, pn = 1;
+            const bool whole = g.M == 0 || g.N == 0 || (Keff == 0 && g.beta == 1.0) ||
+                               (choose_split(g, 4, Keff, cap, kTcPackRows, kTcPackCols, pm, pn) && pm * pn == 1);
+            (whole ? dst : dlg).push_back(g);
+            (whole ? ist : ilg).push_back(gi);
+        }
+        if (!dlg.empty()) {
+            iaat_plan_t a = nullptr, b = nullptr;
+            iaat_status_t st = plan_create_impl(dst.data(), (int64_t)dst.size(), dt, precision, opts, nullptr, &a,
+                                                ist.data(), false);
+            if (st != IAAT_OK)
+                return st;
+            iaat_plan_options_t o = opts ? *opts : iaat_plan_options_t{};
+            o.inject_fault = 0;
+            st = plan_create_tw(dlg.data(), (int64_t)dlg.size(), precision, &o, &b, ilg.data());
+            if (st != IAAT_OK) {
+                iaat_plan_destroy(a);
+                return st;
+            }
+            chain_plan(a, b);
+            a->info.instances = count;
+            if (dst.empty())
+                a->info.kernel_family = 3;
+            *out = a;
+            return IAAT_OK;
+        }
+    }
 
     std::vector<HostTask> tasks;
     tasks.reserve((size_t)count);
@@ -1740,19 +1814,8 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         iaat_plan_destroy(main_plan);
         return st;
     }
-    main_plan->sub = sub;
-    iaat_plan_info_t &a = main_plan->info;
-    const iaat_plan_info_t &b = sub->info;
-    a.instances = count;
-    a.active += b.active;
-    a.tasks += b.tasks;
-    a.groups += b.groups;
-    a.blocks += b.blocks;
-    a.flops += b.flops;
-    a.algorithmic_bytes += b.algorithmic_bytes;
-    a.plan_bytes += b.plan_bytes;
-    a.grid = std::max(a.grid, b.grid);
-    a.kernels += b.kernels;
+    chain_plan(main_plan, sub);
+    main_plan->info.instances = count;
     *out = main_plan;
     return IAAT_OK;
 }

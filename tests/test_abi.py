@@ -74,10 +74,12 @@ def test_domain_boundary_is_inclusive(L):
 @pytest.mark.parametrize("K", [20000, 40000])
 def test_plan_create_rejects_unstageable_k(L, K):
     """1 x 1 x K is small (MNK <= 512000) but a row of A and a column of B
-    that long do not fit one pipeline stage of the tensor-core kernel or of
-    the stage-program CUDA-core kernel, and those never cut K: rejected with
-    UNSUPPORTED, before any device work."""
-    for prec, kernel in ((1, 0), (0, 1)):
+    that long do not fit one pipeline stage of the stage-program kernels
+    (tensor-core or CUDA-core), and those never cut K: a plan on them alone
+    (kernel = 1) is rejected with UNSUPPORTED, before any device work.  (A
+    default tensor-core plan sends such an instance to the warp-tile kernel,
+    which stages K in pieces; the GPU tests cover that.)"""
+    for prec, kernel in ((1, 1), (0, 1)):
         with pytest.raises(iaat.IaatError) as e:
             iaat.iaat_plan_create(_desc(M=1, N=1, K=K, lda=1, ldb=K, ldc=1), iaat.IAAT_F32, prec, kernel=kernel)
         assert e.value.status == 4

@@ -116,13 +116,17 @@ def test_edge_cases(prec):
     assert padding_untouched(b, C)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", sorted(PRECS))
-def test_instances_cut_into_pieces(prec):
-    """Rows and columns beyond one 128 x 128 MMA tile: every piece is its own
-    task of at most 128 x 128.  Integer inputs, so every path is exact."""
+def test_instances_cut_into_pieces(prec, kernel):
+    """Rows and columns beyond one 128 x 128 MMA tile or one stage: on the
+    stage programs alone (kernel 1) every piece is its own task of at most
+    128 x 128; a default plan (kernel 0) sends such instances to the
+    warp-tile kernel, which cuts them into blocks of at most 32 x 32 and
+    stages K in pieces.  Integer inputs, so every path is exact."""
     from .test_gemm_gpu import piece_batch
     b = piece_batch(np.float32, 15)
-    C, info = run_grouped(b, PRECS[prec])
+    C, info = run_grouped(b, PRECS[prec], kernel=kernel)
     assert info["tasks"] > b.count
     err = compare(b, C)
     assert err["exact"], err
@@ -174,7 +178,9 @@ def test_3xbf16_routed_small_k(cuda):
         out[name] = (tC.cpu().numpy(), iaat.iaat_plan_info(plan))
         plan.destroy()
     C, info = out["routed"]
-    assert info["kernels"] == 2 and info["instances"] == b.count
+    # the tensor-core part's launches (stage programs, and the warp-tile
+    # kernel for instances a stage cannot hold) plus the FP32 launch
+    assert info["kernels"] == out["tc"][1]["kernels"] + 1 and info["instances"] == b.count
     assert info["flops"] == out["tc"][1]["flops"]
     err = compare(b, C)
     assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= 1e-5, err
@@ -245,3 +251,29 @@ def test_empty_plans(cuda):
         info = iaat.iaat_plan_info(plan)
         assert info["instances"] == 0 and info["flops"] == 0
         plan.destroy()
+
+
+def test_instances_beyond_a_stage_go_to_the_warp_tile_kernel(cuda):
+    """A default tensor-core plan keeps the instances a stage holds whole on
+    the stage programs and sends the others (64^3 here) to the warp-tile
+    kernel, launched after it: two launches, every instance within the
+    bound, and each part bit for bit what its own kernel's plan gives."""
+    rng = np.random.default_rng(27)
+    n = 1200
+    big = rng.random(n) < 0.25
+    M = np.where(big, 64, rng.integers(1, 33, n))
+    N = np.where(big, 64, rng.integers(1, 33, n))
+    K = np.where(big, 64, rng.integers(8, 33, n))
+    b = W.make_batch(M, N, K, rng.integers(0, 2, n) * 0, rng.integers(0, 2, n), rng.uniform(-2, 2, n),
+                     rng.uniform(-2, 2, n), np.float32, rng, pad=rng.integers(0, 4, (n, 3)))
+    assert W.in_domain(b.M, b.N, b.K, b.transA, b.transB).all()
+    C, info = run_grouped(b, iaat.IAAT_PREC_3XBF16)
+    assert info["kernels"] == 2 and info["kernel_family"] == 1
+    err = compare(b, C)
+    assert err["eps_batch"] <= 1e-5, err
+    assert padding_untouched(b, C)
+    from .gpu_util import gather_index
+    for kernel, idx in ((1, np.nonzero(~big)[0]), (3, np.nonzero(big)[0])):
+        ref, _ = run_grouped(b, iaat.IAAT_PREC_3XBF16, kernel=kernel)
+        gi, _ = gather_index(b, "C", idx)
+        assert np.array_equal(C[gi].view(np.uint32), ref[gi].view(np.uint32)), kernel
