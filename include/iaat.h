@@ -245,8 +245,9 @@ iaat_status_t iaat_gemm_grouped_noalloc(const iaat_gemm_desc_t *descs, int64_t c
  * dtypes: iaat_plan_create_complex; here IAAT_ERR_INVALID_VALUE).
  * A default tensor-core plan (opts NULL or kernel 0, on the stage programs)
  * sends the instances a pipeline stage cannot hold whole to the warp-tile
- * kernel, which stages K in pieces; one iaat_gemm_grouped then launches both
- * (iaat_plan_info: kernels).  On the stage programs alone (kernel 1) such
+ * kernel, which stages K in pieces, when they carry at least a quarter of the
+ * batch's bytes; one iaat_gemm_grouped then launches both (iaat_plan_info:
+ * kernels).  On the stage programs alone (kernel 1) such
  * instances are cut into row / column pieces, and one whose row of A and
  * column of B do not fit a stage (e.g. 1 x 1 x 20000) is rejected with
  * IAAT_ERR_UNSUPPORTED. */

@@ -1592,10 +1592,14 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     // into row / column pieces, each re-reading the shared operand -- to the
     // warp-tile kernel, which stages K in pieces instead (64^3 same-size
     // batches 2.6x faster there); that plan runs after this one on the same
-    // stream.
+    // stream.  Only when they carry at least a quarter of the batch's bytes:
+    // a second launch for a few of them costs more than their pieces (the
+    // uneven batch, 0.1 % of its instances and 1.5 % of its bytes: 0.77 ->
+    // 0.80 ms when split).
     if (tc && split_large && (!opts || opts->kernel == 0) && opts_force_free(opts)) {
         std::vector<iaat_gemm_desc_t> dst, dlg;
         std::vector<int64_t> ist, ilg;
+        double all_bytes = 0.0, large_bytes = 0.0;
         for (int64_t i = 0; i < count; ++i) {
             const iaat_gemm_desc_t &g = descs[i];
             const int64_t gi = index_map ? index_map[i] : i;
@@ -1609,8 +1613,14 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
                                (choose_split(g, 4, Keff, cap, kTcPackRows, kTcPackCols, pm, pn) && pm * pn == 1);
             (whole ? dst : dlg).push_back(g);
             (whole ? ist : ilg).push_back(gi);
+            if (g.M > 0 && g.N > 0) {
+                const double bytes = 4.0 * ((double)g.M * Keff + (double)Keff * g.N + 2.0 * g.M * g.N);
+                all_bytes += bytes;
+                if (!whole)
+                    large_bytes += bytes;
+            }
         }
-        if (!dlg.empty()) {
+        if (!dlg.empty() && large_bytes >= 0.25 * all_bytes) {
             iaat_plan_t a = nullptr, b = nullptr;
             iaat_status_t st = plan_create_impl(dst.data(), (int64_t)dst.size(), dt, precision, opts, nullptr, &a,
                                                 ist.data(), false);
