@@ -1337,11 +1337,13 @@ static double tw_task_cost(const TwTask &t)
     return c + 16.0 * std::ceil(slots / 16.0 / 32.0);
 }
 
-// Stage an operand block as one span when that takes no more ring bytes
-// than staging it run by run.
-static bool tw_span(int runs, int len, int64_t ld)
+// Stage an operand block as one span (one bulk copy, issued by one lane)
+// when that takes at most twice the ring bytes of staging it run by run
+// (each run by the lanes' own copies) and at most a quarter of the ring.
+static bool tw_span(int runs, int len, int64_t ld, uint32_t cap)
 {
-    return tw_op_bytes(runs, len, ld, true) <= tw_op_bytes(runs, len, ld, false);
+    const uint32_t sb = tw_op_bytes(runs, len, ld, true);
+    return sb <= 2 * tw_op_bytes(runs, len, ld, false) && sb <= cap / 2;
 }
 
 static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count, iaat_precision_t precision,
@@ -1403,11 +1405,11 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
                 int kseg = K > 0 ? std::min(((K + 15) / 16) * 16, 16 * 255) : 16;
                 for (int pass = 0; pass < 2; ++pass) {
                     const int kl = std::min(K, kseg);
-                    t.flags = (uint8_t)((readc ? kFlagReadC : 0) | (tw_span(nw, mh, g.ldc) ? kTwSpanC : 0));
+                    t.flags = (uint8_t)((readc ? kFlagReadC : 0) | (tw_span(nw, mh, g.ldc, cap) ? kTwSpanC : 0));
                     if (K > 0) {
-                        if (g.transA ? tw_span(mh, kl, g.lda) : tw_span(kl, mh, g.lda))
+                        if (g.transA ? tw_span(mh, kl, g.lda, cap) : tw_span(kl, mh, g.lda, cap))
                             t.flags |= kTwSpanA;
-                        if (g.transB ? tw_span(kl, nw, g.ldb) : tw_span(nw, kl, g.ldb))
+                        if (g.transB ? tw_span(kl, nw, g.ldb, cap) : tw_span(nw, kl, g.ldb, cap))
                             t.flags |= kTwSpanB;
                         while (kseg > 16 && tw_ab_item_bytes(t, std::min(K, kseg)) > cap)
                             kseg -= 16;

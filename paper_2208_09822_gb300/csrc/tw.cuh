@@ -58,7 +58,8 @@ constexpr uint32_t kTwTmemAlloc = 512;
 // shared memory: the warps' mbarriers and the tensor-memory slot, then the
 // B tiles (one region per term), the warps' task-record rings, the warps'
 // staging rings
-constexpr int kTwCtl = 1024;
+constexpr int kTwCtl = 2048;
+constexpr int kTwItemBars = 1024;   // per warp kTwMaxOut mbarriers: staging item i landed (slot i mod kTwMaxOut)
 constexpr int kTwRecSlots = 32;   // task records a warp holds (a power of two)
 constexpr int kTwRecAhead = 9;    // records are copied this many tasks ahead of their staging
 template <int P> IAAT_CE int tw_opB() { return kTwCtl; }
@@ -69,7 +70,8 @@ static_assert(kTwWarps % 4 == 0 && kTwBlockM == 32 && (kTwBlockN == 16 || kTwBlo
               "quads of warps, one lane quarter per block, MMA N of 16 or 32");
 static_assert(tw_tmem_cols<kTc6xBF16>() <= (int)kTwTmemAlloc && tw_tmem_cols<kTcTF32>() <= (int)kTwTmemAlloc,
               "tensor-memory columns");
-static_assert(kTwMaxOut == 8, "queue slots in lanes 0..7, cp.async groups");
+static_assert(kTwMaxOut == 8, "queue slots in lanes 0..7");
+static_assert(kTwItemBars + kTwWarps * kTwMaxOut * 8 <= kTwCtl, "control area");
 // The record of task t is copied in the cp.async group of task t - 9's first
 // item.  When task t is begun, at most kTwMaxOut items are in flight and the
 // first items of tasks t-8 .. t-1 came after that one, so the consumer has
@@ -107,28 +109,13 @@ __device__ __forceinline__ void tw_copy_runs(uint32_t dst, const char *src, int6
     }
 }
 
-// Copy `bytes` bytes from global address src as the 16-byte granules that
-// cover them, to dst (the first byte lands at dst + (src & 15)).
-__device__ __forceinline__ void tw_copy_span(uint32_t dst, const char *src, int64_t bytes, int lane)
+// The 16-byte granules that cover `bytes` bytes from global address src:
+// their aligned start, and their count times 16.
+__device__ __forceinline__ void tw_span_granules(const char *src, int64_t bytes, const char **a, uint32_t *n)
 {
     const uintptr_t s = reinterpret_cast<uintptr_t>(src);
-    const uintptr_t a = s & ~(uintptr_t)15;
-    const int n = (int)(((int64_t)(s & 15u) + bytes + 15) >> 4);
-    for (int e = lane; e < n; e += 32)
-        cp_async16(dst + 16u * (uint32_t)e, reinterpret_cast<const void *>(a + 16u * (uint32_t)e));
-}
-
-// Stage one operand block: R runs of len elements, ld elements apart, the
-// first at src; as one span or run by run (tw_op_bytes).
-__device__ __forceinline__ void tw_copy_op(uint32_t dst, const char *src, int64_t ld, int R, int len, bool span,
-                                           int lane)
-{
-    if (R <= 0 || len <= 0)
-        return;
-    if (span)
-        tw_copy_span(dst, src, 4 * ((int64_t)(R - 1) * ld + len), lane);
-    else
-        tw_copy_runs(dst, src, 4 * ld, R, 4 * len, lane);
+    *a = reinterpret_cast<const char *>(s & ~(uintptr_t)15);
+    *n = (uint32_t)((((int64_t)(s & 15u) + bytes + 15) >> 4) << 4);
 }
 
 // The task the warp is computing, from the record at the start of its first item.
@@ -394,6 +381,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
     if (threadIdx.x == 0) {
         for (int w = 0; w < kTwWarps; ++w)
             mbar_init(sb + 8u * (uint32_t)w, 1);
+        // one arrival by lane 0 (with the bulk copies' byte count); the
+        // lanes' cp.async copies are tracked by arrivals that add their own
+        for (int i = 0; i < kTwWarps * kTwMaxOut; ++i)
+            mbar_init(sb + (uint32_t)(kTwItemBars + 8 * i), 1);
         fence_barrier_init();
     }
     if (warp == 0)
@@ -410,6 +401,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
     const uint32_t bw = sb + (uint32_t)(tw_opB<P>() + warp * tw_tile<P>());
     const char *ring = smem + tw_ring_off<P>() + warp * (int)RING;
     const uint32_t ring_s = sb + (uint32_t)tw_ring_off<P>() + (uint32_t)warp * RING;
+    const uint32_t ibar = sb + (uint32_t)(kTwItemBars + 8 * kTwMaxOut * warp);   // + 8 * slot
 
     const int gw = (int)blockIdx.x * kTwWarps + warp;
     int it = 0, te = 0;
@@ -506,6 +498,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         }
         uint32_t d = ring_s + off;
         const int nops = citem ? 1 : (kl > 0 ? 2 : 0);
+        // spans go as bulk copies issued by lane 0 below, runs as the lanes'
+        // cp.async; item completion: the slot's mbarrier
+        const char *bsrc[2] = {nullptr, nullptr};
+        uint32_t bdst[2] = {0u, 0u}, bn[2] = {0u, 0u};
         for (int o = 0; o < nops; ++o) {
             const bool isb = o == 1;
             const int tr = citem ? 0 : (isb ? ir.tb : ir.ta);
@@ -518,10 +514,25 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
             const char *src = citem ? base : base + 4 * (krun ? (int64_t)k0 * ld : (int64_t)k0);
             const int R = citem ? ir.N : (krun ? kl : rows);
             const int len = citem ? ir.M : (krun ? rows : kl);
-            tw_copy_op(d, src, ld, R, len, span, lane);
+            if (R > 0 && len > 0) {
+                if (span) {
+                    tw_span_granules(src, 4 * ((int64_t)(R - 1) * ld + len), &bsrc[o], &bn[o]);
+                    bdst[o] = d;
+                } else {
+                    tw_copy_runs(d, src, 4 * ld, R, 4 * len, lane);
+                }
+            }
             d += tw_op_bytes(R, len, ld, span);
         }
-        cp_async_commit();
+        const uint32_t bar_i = ibar + 8u * (uint32_t)(issued & (kTwMaxOut - 1));
+        asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar_i) : "memory");
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar_i, bn[0] + bn[1]);
+            for (int o = 0; o < 2; ++o)
+                if (bn[o])
+                    bulk_g2s(bdst[o], bsrc[o], bn[o], bar_i);
+        }
         if (lane == (issued & (kTwMaxOut - 1))) {
             q_off = off;
             q_end = head;
@@ -563,8 +574,12 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         const uint32_t fl = __shfl_sync(0xffffffffu, q_fl, s);
         const int k0 = __shfl_sync(0xffffffffu, q_k0, s), k1 = __shfl_sync(0xffffffffu, q_k1, s);
         const int ct = __shfl_sync(0xffffffffu, q_t, s);
-        cp_async_wait_upto(issued - consumed - 1);
-        __syncwarp();
+        if (!warp_wait(ibar + 8u * (uint32_t)s, (uint32_t)((consumed / kTwMaxOut) & 1))) {
+            if (lane == 0)
+                set_error(p.err, kErrTimeoutFull);
+            abort = true;
+            break;
+        }
         const char *item = ring + off;
         if (!(fl & kTwCItem)) {
             const char *sec = item;
@@ -623,6 +638,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) tw_kernel(const TwParams p)
         tail = end;
         ++consumed;
     }
+    // after a time-out, wait (bounded) for the copies still in flight into
+    // this warp's ring before the CTA's shared memory is given up
+    for (int i = consumed; abort && i < issued; ++i)
+        mbar_wait(ibar + 8u * (uint32_t)(i & (kTwMaxOut - 1)), (uint32_t)((i / kTwMaxOut) & 1), kWaitLimitNs);
     cp_async_wait<0>();
     wait_mma();
     tc_fence_before();
