@@ -442,6 +442,79 @@ static int stage_min_blocks(const TaskDesc &d, int dt, uint32_t cap)
 // markers (alpha 0 or 1; beta 0, 1 or 2 for "other"), and each task's alpha
 // field holds the instance index, which build_programs turns into the address
 // of the instance's entry in the plan's scalar table.
+static void push_task(int64_t idx, const iaat_gemm_desc_t &g, int dt, int Keff, int r0, int h, int c0, int w,
+                      const TileChoice &t, std::vector<HostTask> &out, int64_t *blocks_out)
+{
+    const int esz = dtype_esz(dt);
+    TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
+    if (is_complex(dt)) {
+        d.alpha = (double)idx;
+        d.beta = 0.0;
+    }
+    d.variant = (uint8_t)t.variant;
+    d.nbm = (uint8_t)t.nbm;
+    d.nbn = (uint8_t)t.nbn;
+    const TaskStages st = plan_task(d, esz);
+    *blocks_out += (int64_t)d.nbm * d.nbn;
+    out.push_back(HostTask{d, st.total(), (double)(st.a.tx + st.b.tx + st.c.tx) + tuning().cost_per_slot * t.cost});
+}
+
+// Mixed-shape tiling of one instance (Sec. V-A: one C tiled with several
+// block shapes, the cheapest under the cost model), for the DFMA-bound types,
+// where the idle lanes of a partly filled register tile still cost DFMA
+// slots: besides the uniform grid of one variant, C may be cut into a part
+// that is an exact multiple of a variant's block width (or height) and a
+// remainder, each tiled with its own variant, when the model says that is at
+// least 3 % cheaper (the remainder is a task of its own and stages its
+// operands again).
+static iaat_status_t make_mixed_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, int Keff, uint32_t cap,
+                                      std::vector<HostTask> &out, int64_t *blocks_out)
+{
+    const int M = g.M, N = g.N, esz = dtype_esz(dt);
+    auto choose = [&](int r0, int h, int c0, int w) {
+        const TaskDesc d = make_piece(g, esz, Keff, r0, h, c0, w);
+        return choose_tiling(dt, h, w, Keff, -1, true, stage_min_blocks(d, dt, cap));
+    };
+    const TileChoice whole = choose(0, M, 0, N);
+    double best = 0.97 * whole.cost;
+    int split = 0;   // > 0: columns [0, split) and [split, N); < 0: rows [0, -split) and [-split, M)
+    TileChoice ta{}, tb{};
+    int nv;
+    const Variant *vs = variants(dt, &nv);
+    for (int v = 0; v < nv; ++v) {
+        const int bn = vs[v].ln * vs[v].nr, bm = vs[v].lm * vs[v].mr;
+        const int w1 = (N / bn) * bn, h1 = (M / bm) * bm;
+        if (w1 > 0 && w1 < N) {
+            const TileChoice a = choose(0, M, 0, w1), b = choose(0, M, w1, N - w1);
+            if (a.cost + b.cost < best) {
+                best = a.cost + b.cost;
+                split = w1;
+                ta = a;
+                tb = b;
+            }
+        }
+        if (h1 > 0 && h1 < M) {
+            const TileChoice a = choose(0, h1, 0, N), b = choose(h1, M - h1, 0, N);
+            if (a.cost + b.cost < best) {
+                best = a.cost + b.cost;
+                split = -h1;
+                ta = a;
+                tb = b;
+            }
+        }
+    }
+    if (split > 0) {
+        push_task(idx, g, dt, Keff, 0, M, 0, split, ta, out, blocks_out);
+        push_task(idx, g, dt, Keff, 0, M, split, N - split, tb, out, blocks_out);
+    } else if (split < 0) {
+        push_task(idx, g, dt, Keff, 0, -split, 0, N, ta, out, blocks_out);
+        push_task(idx, g, dt, Keff, -split, M + split, 0, N, tb, out, blocks_out);
+    } else {
+        push_task(idx, g, dt, Keff, 0, M, 0, N, whole, out, blocks_out);
+    }
+    return IAAT_OK;
+}
+
 iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc, int force_variant, uint32_t cap,
                          std::vector<HostTask> &out, int64_t *blocks_out, int piece = 0)
 {
@@ -458,6 +531,8 @@ iaat_status_t make_tasks(int64_t idx, const iaat_gemm_desc_t &g, int dt, bool tc
     if (!choose_split(g, esz, Keff, cap, mcap, ncap, pm, pn))
         return fail(IAAT_ERR_UNSUPPORTED, "instance %lld: operands do not fit a pipeline stage (M=%d N=%d K=%d)",
                     (long long)idx, M, N, g.K);
+    if (pm * pn == 1 && !tc && piece == 0 && force_variant < 0 && (dt == IAAT_F64 || dt == IAAT_C64))
+        return make_mixed_tasks(idx, g, dt, Keff, cap, out, blocks_out);
     for (int i = 0; i < pm; ++i) {
         int r0, h;
         piece_range(M, pm, i, r0, h);

@@ -248,3 +248,24 @@ def test_injected_fault_is_reported_and_context_survives(cuda):
     # the context still works
     C, _ = run_grouped(b)
     assert compare(b, C)["eps_batch"] <= 1e-5
+
+
+def test_fp64_mixed_tiling_exact():
+    """FP64 instances shaped like the fc64 batch (M in {32, 64}, N and K up
+    to 80): where the cost model prefers it, C is cut into an exact multiple
+    of a wide block and a remainder, each with its own register-tile variant
+    (mixed-shape tiling, Sec. V-A); some instances here are cut that way.
+    Integer inputs, so the result is exact."""
+    rng = np.random.default_rng(41)
+    n = 300
+    M = rng.choice(np.array([32, 64]), n)
+    N = rng.integers(8, 81, n)
+    K = rng.integers(8, 81, n)
+    b = W.make_batch(M, N, K, rng.integers(0, 2, n) * 0, rng.integers(0, 2, n), rng.choice([1.0, -1.0], n),
+                     rng.choice([0.0, 1.0], n), np.float64, rng, pad=rng.integers(0, 4, (n, 3)), dist="int")
+    assert W.in_domain(b.M, b.N, b.K, b.transA, b.transB).all()
+    C, info = run_grouped(b)
+    assert info["tasks"] > info["active"], info
+    err = compare(b, C)
+    assert err["exact"], err
+    assert padding_untouched(b, C)
