@@ -1667,16 +1667,17 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     if (tc && kernel == 2)
         return plan_create_tc2(descs, count, precision, opts, out, index_map);
 
-    // A default tensor-core plan on the stage programs sends the instances
-    // that a stage cannot hold whole -- the ones the stage programs would cut
-    // into row / column pieces, each re-reading the shared operand -- to the
-    // warp-tile kernel, which stages K in pieces instead (64^3 same-size
-    // batches 2.6x faster there); that plan runs after this one on the same
-    // stream.  Only when they carry at least a quarter of the batch's bytes:
+    // A default FP32 plan on the stage programs sends the instances that a
+    // stage cannot hold whole -- the ones the stage programs would cut into
+    // row / column pieces, each re-reading the shared operand -- to a kernel
+    // that stages K in pieces instead: the warp-tile kernel for tensor-core
+    // precisions (same-size 64^3 batches 2.6x faster there), the warp-stream
+    // kernel for FFMA (80^3 1.45x faster); that plan runs after this one on
+    // the same stream.  Only when they carry at least a quarter of the batch's bytes:
     // a second launch for a few of them costs more than their pieces (the
     // uneven batch, 0.1 % of its instances and 1.5 % of its bytes: 0.77 ->
     // 0.80 ms when split).
-    if (tc && split_large && (!opts || opts->kernel == 0) && opts_force_free(opts)) {
+    if (dt == IAAT_F32 && split_large && (!opts || opts->kernel == 0) && opts_force_free(opts)) {
         std::vector<iaat_gemm_desc_t> dst, dlg;
         std::vector<int64_t> ist, ilg;
         double all_bytes = 0.0, large_bytes = 0.0;
@@ -1690,7 +1691,9 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
             const int Keff = g.alpha == 0.0 ? 0 : g.K;
             int pm = 1, pn = 1;
             const bool whole = g.M == 0 || g.N == 0 || (Keff == 0 && g.beta == 1.0) ||
-                               (choose_split(g, 4, Keff, cap, kTcPackRows, kTcPackCols, pm, pn) && pm * pn == 1);
+                               (choose_split(g, 4, Keff, cap, tc ? kTcPackRows : kPieceRows,
+                                             tc ? kTcPackCols : kPieceCols, pm, pn) &&
+                                pm * pn == 1);
             (whole ? dst : dlg).push_back(g);
             (whole ? ist : ilg).push_back(gi);
             if (g.M > 0 && g.N > 0) {
@@ -1708,7 +1711,8 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
                 return st;
             iaat_plan_options_t o = opts ? *opts : iaat_plan_options_t{};
             o.inject_fault = 0;
-            st = plan_create_tw(dlg.data(), (int64_t)dlg.size(), precision, &o, &b, ilg.data());
+            st = tc ? plan_create_tw(dlg.data(), (int64_t)dlg.size(), precision, &o, &b, ilg.data())
+                    : plan_create_ws(dlg.data(), (int64_t)dlg.size(), &o, -1, &b, ilg.data());
             if (st != IAAT_OK) {
                 iaat_plan_destroy(a);
                 return st;
@@ -1716,7 +1720,7 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
             chain_plan(a, b);
             a->info.instances = count;
             if (dst.empty())
-                a->info.kernel_family = 3;
+                a->info.kernel_family = tc ? 3 : 2;
             *out = a;
             return IAAT_OK;
         }

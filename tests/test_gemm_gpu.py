@@ -149,10 +149,13 @@ def piece_batch(dtype, seed):
     return b
 
 
-@pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_instances_cut_into_pieces(dtype):
+@pytest.mark.parametrize("dtype,kernel", [(np.float32, 0), (np.float32, 1), (np.float64, 0)])
+def test_instances_cut_into_pieces(dtype, kernel):
+    """Instances beyond one stage: on the stage programs (kernel 1, and FP64)
+    cut into row / column pieces; a default FP32 plan sends them to the
+    warp-stream kernel, which streams K.  Integer inputs, exact."""
     b = piece_batch(dtype, 14)
-    C, info = run_grouped(b)
+    C, info = run_grouped(b, kernel=kernel)
     assert info["tasks"] > b.count
     err = compare(b, C)
     assert err["exact"], err
