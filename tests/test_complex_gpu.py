@@ -197,3 +197,23 @@ def test_single_calls(dtype, cuda):
     iaat.iaat_plan_check(None, s)
     C = tC.cpu().numpy()
     _assert_ok(b, C, compare(b, C), TOL[dtype])
+
+
+def test_zgemm_mixed_tiling_exact():
+    """ZGEMM instances whose C the planner cuts into an exact multiple of a
+    block and a remainder, each with its own register tile (mixed-shape
+    tiling for the DFMA-bound types); Gaussian-integer inputs, so every
+    path is exact."""
+    rng = np.random.default_rng(57)
+    n = 400
+    M = rng.integers(1, 81, n)
+    N = rng.integers(1, 81, n)
+    K = rng.integers(1, 41, n)
+    b = W.make_batch(M, N, K, rng.integers(0, 2, n) * 0, rng.integers(0, 2, n), np.ones(n, complex),
+                     np.zeros(n, complex), np.complex128, rng, pad=rng.integers(0, 3, (n, 3)), dist="int")
+    b = b.select(np.nonzero(W.in_domain(b.M, b.N, b.K, b.transA, b.transB))[0])
+    C, info = run_grouped(b)
+    assert info["tasks"] > info["active"], info
+    err = compare(b, C)
+    assert err["exact"], err
+    assert padding_untouched(b, C)

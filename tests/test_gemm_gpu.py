@@ -272,3 +272,29 @@ def test_fp64_mixed_tiling_exact():
     err = compare(b, C)
     assert err["exact"], err
     assert padding_untouched(b, C)
+
+
+def test_ffma_instances_beyond_a_stage_go_to_the_warp_stream_kernel():
+    """A default FP32 plan keeps the instances a stage holds whole on the
+    stage programs and sends the others (80^3 here) to the warp-stream
+    kernel, which streams K: two launches, each part bit for bit what its
+    own kernel's plan gives, the whole within the FP32 bound."""
+    rng = np.random.default_rng(43)
+    n = 600
+    big = rng.random(n) < 0.25
+    M = np.where(big, 80, rng.integers(1, 33, n))
+    N = np.where(big, 80, rng.integers(1, 33, n))
+    K = np.where(big, 80, rng.integers(1, 33, n))
+    b = W.make_batch(M, N, K, rng.integers(0, 2, n) * 0, rng.integers(0, 2, n), rng.uniform(-2, 2, n),
+                     rng.uniform(-2, 2, n), np.float32, rng, pad=rng.integers(0, 4, (n, 3)))
+    assert W.in_domain(b.M, b.N, b.K, b.transA, b.transB).all()
+    C, info = run_grouped(b)
+    assert info["kernels"] == 2 and info["kernel_family"] == 1
+    err = compare(b, C)
+    assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= 1e-5, err
+    assert padding_untouched(b, C)
+    from .gpu_util import gather_index
+    for kernel, idx in ((1, np.nonzero(~big)[0]), (2, np.nonzero(big)[0])):
+        ref, _ = run_grouped(b, kernel=kernel)
+        gi, _ = gather_index(b, "C", idx)
+        assert np.array_equal(C[gi].view(np.uint32), ref[gi].view(np.uint32)), kernel
