@@ -37,7 +37,12 @@ METRIC = "small-GEMM GFLOP/s & roofline % (uneven batch), TC split vs plain FP32
 WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT/TN/TT uniform "
             "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
 NOMINAL_HBM_GBS = 8000.0
-PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4, "3xbf16-k8ffma": 1}
+# paths that route small instances to the FP32 CUDA-core kernel: name ->
+# (route_k_below, route_mnk_below)
+ROUTE = {"3xbf16-k8ffma": (8, 0), "3xbf16-r8": (8, 8 ** 3), "3xbf16-r12": (8, 12 ** 3), "3xbf16-r16": (8, 16 ** 3),
+         "3xbf16-r24": (8, 24 ** 3), "3xbf16-r32": (8, 32 ** 3)}
+PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
+PRECISIONS.update({n: 1 for n in ROUTE})
 # each path can also be forced onto one kernel family: name + "@stage"
 # (stage-program kernels), name + "@stream" (warp-stream / pack-stream) or,
 # for the tensor-core paths, name + "@warp" (warp-tile kernel)
@@ -47,8 +52,6 @@ for _n in list(PRECISIONS):
         PRECISIONS[_n + "@warp"] = PRECISIONS[_n]
 KERNEL = {n: {"stage": 1, "stream": 2, "warp": 3}.get(n.split("@")[1], 0) if "@" in n else 0 for n in PRECISIONS}
 ROUTE_BASE = lambda n: n.split("@")[0]
-# paths that route small-K instances to the FP32 CUDA-core kernel (route_k_below)
-ROUTE = {"3xbf16-k8ffma": 8}
 
 # Batches bench.py can time.  The default is the uneven FP32 batch (the
 # headline); the others run the CUDA-core path of their type only:
@@ -436,11 +439,12 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
-    ap.add_argument("--precision", default="3xbf16", choices=sorted(PRECISIONS),
-                    help="the headline path (the tensor-core FP32 split by default)")
-    ap.add_argument("--compare", default="ffma,3xbf16-k8ffma", type=lambda v: [x for x in v.split(",") if x],
-                    help="comma-separated paths timed beside the headline (plain FP32 and the 3xBF16 plan "
-                         "that routes K < 8 to FP32 by default)")
+    ap.add_argument("--precision", default="3xbf16-r16", choices=sorted(PRECISIONS),
+                    help="the headline path: by default the tensor-core FP32 split (3xBF16) on the instances "
+                         "with M*N*K >= 16^3 and K >= 8, the smaller ones on the FP32 CUDA cores")
+    ap.add_argument("--compare", default="ffma,3xbf16,3xbf16-k8ffma", type=lambda v: [x for x in v.split(",") if x],
+                    help="comma-separated paths timed beside the headline (by default plain FP32, 3xBF16 for "
+                         "every instance, and 3xBF16 with only K < 8 routed to FP32)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="instance ranges the end-to-end leg pipelines copies and launches over")
@@ -539,7 +543,9 @@ def main():
     def make_plan(d, name):
         if wl_dtype == 0:
             return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name],
-                                         route_k_below=ROUTE.get(ROUTE_BASE(name), 0), kernel=KERNEL.get(name, 0))
+                                         route_k_below=ROUTE.get(ROUTE_BASE(name), (0, 0))[0],
+                                         route_mnk_below=ROUTE.get(ROUTE_BASE(name), (0, 0))[1],
+                                         kernel=KERNEL.get(name, 0))
         if wl_dtype == 1:
             return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
         return iaat.iaat_plan_create_complex(d, wl_dtype)

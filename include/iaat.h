@@ -144,7 +144,12 @@ typedef struct {
                                   from tensor memory; the CUDA-core part of a routed
                                   plan then takes the default).  FP64 and complex
                                   plans always run stage programs */
-    int32_t reserved[2];
+    int32_t route_mnk_below;   /* tensor-core plans only: instances with M*N*K below
+                                  this value also run on the FP32 CUDA-core kernel
+                                  (the same second launch as route_k_below); the
+                                  tensor cores then take only the instances large
+                                  enough to fill their tiles.  0: no size routing */
+    int32_t reserved;
 } iaat_plan_options_t;
 
 /* Statistics of a plan (iaat_plan_info). */

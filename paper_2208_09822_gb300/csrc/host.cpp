@@ -1870,7 +1870,9 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         return fail(IAAT_ERR_UNSUPPORTED, "FP64 plans run on the FP64 pipes only");
     if (opts && opts->route_k_below < 0)
         return fail(IAAT_ERR_INVALID_VALUE, "route_k_below %d is negative", opts->route_k_below);
-    if (precision == IAAT_PREC_DEFAULT || !opts || opts->route_k_below == 0)
+    if (opts && opts->route_mnk_below < 0)
+        return fail(IAAT_ERR_INVALID_VALUE, "route_mnk_below %d is negative", opts->route_mnk_below);
+    if (precision == IAAT_PREC_DEFAULT || !opts || (opts->route_k_below == 0 && opts->route_mnk_below == 0))
         return plan_create_impl(descs, count, dtype, precision, opts, nullptr, out);
 
     // Routed tensor-core plan: instances with K below route_k_below (or
@@ -1889,11 +1891,14 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     std::vector<int64_t> itc, ifma;
     for (int64_t i = 0; i < count; ++i) {
         const int keff = descs[i].alpha == 0.0 ? 0 : descs[i].K;
-        (keff < opts->route_k_below ? dfma : dtc).push_back(descs[i]);
-        (keff < opts->route_k_below ? ifma : itc).push_back(i);
+        const bool small = keff < opts->route_k_below ||
+                           (int64_t)descs[i].M * descs[i].N * keff < (int64_t)opts->route_mnk_below;
+        (small ? dfma : dtc).push_back(descs[i]);
+        (small ? ifma : itc).push_back(i);
     }
     iaat_plan_options_t o = *opts;
     o.route_k_below = 0;
+    o.route_mnk_below = 0;
     iaat_plan_t main_plan = nullptr, sub = nullptr;
     iaat_status_t st = plan_create_impl(dtc.data(), (int64_t)dtc.size(), IAAT_F32, precision, &o, nullptr, &main_plan,
                                         itc.data());

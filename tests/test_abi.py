@@ -193,6 +193,13 @@ def test_routed_plan_validates_with_caller_indices(L):
     with pytest.raises(iaat.IaatError) as e:
         iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=-1)
     assert e.value.status == 1
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_mnk_below=-1)
+    assert e.value.status == 1 and "route_mnk_below" in e.value.message
+    # routing by size alone (route_k_below 0) also validates with the caller's index
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(d, iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_mnk_below=4096)
+    assert e.value.status == 1 and "instance 3" in e.value.message
 
 
 def test_pack_create_validates_before_the_device(L):

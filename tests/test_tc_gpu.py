@@ -277,3 +277,36 @@ def test_instances_beyond_a_stage_go_to_the_warp_tile_kernel(cuda):
         ref, _ = run_grouped(b, iaat.IAAT_PREC_3XBF16, kernel=kernel)
         gi, _ = gather_index(b, "C", idx)
         assert np.array_equal(C[gi].view(np.uint32), ref[gi].view(np.uint32)), kernel
+
+
+def test_3xbf16_routed_by_size(cuda):
+    """route_mnk_below: instances with M*N*K below 16^3 (or K below 8) run on
+    the FP32 CUDA-core kernel, the rest as 3xBF16 on the tensor cores: every
+    instance of the uneven batch within 1e-5, and each part bit for bit what
+    the unrouted plan of its own path gives."""
+    torch = cuda
+    b = W.uneven(count=40000, seed=28)
+    tA, tB, tC, descs = to_device(b)
+    C0 = tC.clone()
+    s = torch.cuda.current_stream()
+    out = {}
+    for name, prec, kw in (("routed", iaat.IAAT_PREC_3XBF16, dict(route_k_below=8, route_mnk_below=16 ** 3)),
+                           ("tc", iaat.IAAT_PREC_3XBF16, {}), ("fma", iaat.IAAT_PREC_DEFAULT, {})):
+        tC.copy_(C0)
+        plan = iaat.iaat_plan_create(descs, iaat.IAAT_F32, prec, **kw)
+        iaat.iaat_gemm_grouped(plan, s)
+        iaat.iaat_plan_check(plan, s)
+        out[name] = (tC.cpu().numpy(), iaat.iaat_plan_info(plan))
+        plan.destroy()
+    C, info = out["routed"]
+    assert info["instances"] == b.count and info["flops"] == out["tc"][1]["flops"]
+    err = compare(b, C)
+    assert err["eps_batch"] <= 1e-5 and err["eps_inst_max"] <= 1e-5, err
+    assert padding_untouched(b, C)
+    from .gpu_util import gather_index
+    keff = np.where(b.alpha == 0, 0, b.K).astype(np.int64)
+    small = np.nonzero((keff < 8) | (b.M.astype(np.int64) * b.N * keff < 16 ** 3))[0]
+    large = np.setdiff1d(np.arange(b.count), small)
+    for idx, ref in ((small, out["fma"][0]), (large, out["tc"][0])):
+        gi, _ = gather_index(b, "C", idx)
+        assert np.array_equal(C[gi].view(np.uint32), ref[gi].view(np.uint32))
