@@ -38,19 +38,26 @@ WORKLOAD = ("uneven-{n}-fp32: {n} instances, M,N,K log-uniform int [1,80], NN/NT
             "(TN redrawn to MNK<=32768), ld=rows+U{{0..7}}, alpha,beta~U[-2,2], N(0,1), seed 2")
 NOMINAL_HBM_GBS = 8000.0
 # paths that route small instances to the FP32 CUDA-core kernel: name ->
-# (route_k_below, route_mnk_below)
-ROUTE = {"3xbf16-k8ffma": (8, 0), "3xbf16-r8": (8, 8 ** 3), "3xbf16-r12": (8, 12 ** 3), "3xbf16-r16": (8, 16 ** 3),
-         "3xbf16-r24": (8, 24 ** 3), "3xbf16-r32": (8, 32 ** 3)}
+# (route_k_below, route_mnk_below, route_kernel); "d": the CUDA-core part on
+# the warp-direct kernel
+ROUTE = {"3xbf16-k8ffma": (8, 0, 0), "3xbf16-r8": (8, 8 ** 3, 0), "3xbf16-r12": (8, 12 ** 3, 0),
+         "3xbf16-r16": (8, 16 ** 3, 0), "3xbf16-r24": (8, 24 ** 3, 0), "3xbf16-r32": (8, 32 ** 3, 0)}
+ROUTE.update({"3xbf16-k8d": (8, 0, 4)})
+ROUTE.update({f"3xbf16-r{n}d": (8, n ** 3, 4) for n in (8, 12, 16, 20, 24, 32)})
 PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
 PRECISIONS.update({n: 1 for n in ROUTE})
 # each path can also be forced onto one kernel family: name + "@stage"
-# (stage-program kernels), name + "@stream" (warp-stream / pack-stream) or,
-# for the tensor-core paths, name + "@warp" (warp-tile kernel)
+# (stage-program kernels), name + "@stream" (warp-stream / pack-stream), for
+# the tensor-core paths name + "@warp" (warp-tile kernel), for FFMA name +
+# "@direct" (warp-direct kernel)
 for _n in list(PRECISIONS):
     PRECISIONS[_n + "@stage"] = PRECISIONS[_n + "@stream"] = PRECISIONS[_n]
     if PRECISIONS[_n]:
         PRECISIONS[_n + "@warp"] = PRECISIONS[_n]
-KERNEL = {n: {"stage": 1, "stream": 2, "warp": 3}.get(n.split("@")[1], 0) if "@" in n else 0 for n in PRECISIONS}
+    else:
+        PRECISIONS[_n + "@direct"] = PRECISIONS[_n]
+KERNEL = {n: {"stage": 1, "stream": 2, "warp": 3, "direct": 4}.get(n.split("@")[1], 0) if "@" in n else 0
+          for n in PRECISIONS}
 ROUTE_BASE = lambda n: n.split("@")[0]
 
 # Batches bench.py can time.  The default is the uneven FP32 batch (the
@@ -126,7 +133,7 @@ def kernel_unit(precision, family=None):
     if family is None:
         family = KERNEL.get(precision, 0) or 1
     if base in ("ffma", "dfma"):
-        return "kernels_ws.cu" if family == 2 else KERNEL_UNITS[base]
+        return {2: "kernels_ws.cu", 4: "kernels_wd.cu"}.get(family, KERNEL_UNITS[base])
     if base in KERNEL_UNITS:
         return KERNEL_UNITS[base]
     return {2: "kernels_tc2.cu", 3: "kernels_tw.cu"}.get(family, "kernels_tc.cu")
@@ -136,9 +143,12 @@ def kernel_source_hash(precision="3xbf16", family=None):
     """Hash of the sources a path's kernel is compiled from: its translation
     unit and every header it includes (launch.h, which only declares the
     host launchers, aside), so a profile stays current while that kernel's
-    code is unchanged."""
+    code is unchanged.  A routed path hashes its CUDA-core kernel's sources
+    too: its launches run both."""
     csrc = os.path.join(ROOT, "paper_2208_09822_gb300", "csrc")
     seen, todo = set(), [kernel_unit(precision, family)]
+    if ROUTE_BASE(precision) in ROUTE:
+        todo.append("kernels_wd.cu" if ROUTE[ROUTE_BASE(precision)][2] == 4 else KERNEL_UNITS["ffma"])
     while todo:
         f = todo.pop()
         if f in seen or f == "launch.h" or not os.path.exists(os.path.join(csrc, f)):
@@ -439,12 +449,15 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
-    ap.add_argument("--precision", default="3xbf16-r16", choices=sorted(PRECISIONS),
+    ap.add_argument("--precision", default="3xbf16-r20d", choices=sorted(PRECISIONS),
                     help="the headline path: by default the tensor-core FP32 split (3xBF16) on the instances "
-                         "with M*N*K >= 16^3 and K >= 8, the smaller ones on the FP32 CUDA cores")
-    ap.add_argument("--compare", default="ffma,3xbf16,3xbf16-k8ffma", type=lambda v: [x for x in v.split(",") if x],
-                    help="comma-separated paths timed beside the headline (by default plain FP32, 3xBF16 for "
-                         "every instance, and 3xBF16 with only K < 8 routed to FP32)")
+                         "with M*N*K >= 20^3 and K >= 8, the smaller ones on the FP32 CUDA cores (warp-direct "
+                         "kernel)")
+    ap.add_argument("--compare", default="ffma,ffma@direct,3xbf16,3xbf16-r16",
+                    type=lambda v: [x for x in v.split(",") if x],
+                    help="comma-separated paths timed beside the headline (by default plain FP32 on the stage "
+                         "programs and on the warp-direct kernel, 3xBF16 for every instance, and 3xBF16 with "
+                         "the small instances on the stage programs)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="instance ranges the end-to-end leg pipelines copies and launches over")
@@ -542,10 +555,9 @@ def main():
 
     def make_plan(d, name):
         if wl_dtype == 0:
-            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name],
-                                         route_k_below=ROUTE.get(ROUTE_BASE(name), (0, 0))[0],
-                                         route_mnk_below=ROUTE.get(ROUTE_BASE(name), (0, 0))[1],
-                                         kernel=KERNEL.get(name, 0))
+            rk, rm, rf = ROUTE.get(ROUTE_BASE(name), (0, 0, 0))
+            return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name], route_k_below=rk, route_mnk_below=rm,
+                                         route_kernel=rf, kernel=KERNEL.get(name, 0))
         if wl_dtype == 1:
             return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
         return iaat.iaat_plan_create_complex(d, wl_dtype)

@@ -142,14 +142,22 @@ typedef struct {
                                   precisions only: every warp stages, converts and
                                   multiplies its own blocks of at most 32 x 32, op(A)
                                   from tensor memory; the CUDA-core part of a routed
-                                  plan then takes the default).  FP64 and complex
-                                  plans always run stage programs */
+                                  plan then takes the default), 4 = the warp-direct
+                                  CUDA-core kernel (FP32 or FP64 plans of the default
+                                  precision: every warp runs its own blocks of at most
+                                  32 rows straight from global memory, no staging
+                                  pipeline; for batches of tiny instances).  Complex
+                                  plans always run stage programs, FP64 plans stage
+                                  programs unless 4 is asked for */
     int32_t route_mnk_below;   /* tensor-core plans only: instances with M*N*K below
                                   this value also run on the FP32 CUDA-core kernel
                                   (the same second launch as route_k_below); the
                                   tensor cores then take only the instances large
                                   enough to fill their tiles.  0: no size routing */
-    int32_t reserved;
+    int32_t route_kernel;      /* routed tensor-core plans: the kernel family of the
+                                  CUDA-core part (values as for kernel: 1, 2 or 4);
+                                  0: the main plan's family when that is 1 or 2,
+                                  else the default */
 } iaat_plan_options_t;
 
 /* Statistics of a plan (iaat_plan_info). */
@@ -169,8 +177,8 @@ typedef struct {
                                   tensor-core plan routes small-K instances) */
     int32_t dtype, precision;
     int32_t kernel_family;     /* the kernels the plan runs: 1 stage programs, 2 stream
-                                  (warp-stream / pack-stream), 3 warp-tile; for a routed
-                                  plan, its tensor-core part's */
+                                  (warp-stream / pack-stream), 3 warp-tile, 4 warp-direct;
+                                  for a routed plan, its tensor-core part's */
     int32_t reserved;
 } iaat_plan_info_t;
 

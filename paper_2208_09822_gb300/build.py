@@ -15,7 +15,8 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_fma.cu", "kernels_ws.cu", "kernels_tc.cu", "kernels_tc2.cu", "kernels_tw.cu", "kernels_cplx.cu",
+CU_SOURCES = ["kernels_fma.cu", "kernels_ws.cu", "kernels_tc.cu", "kernels_tc2.cu", "kernels_tw.cu", "kernels_wd.cu",
+              "kernels_cplx.cu",
               "pack.cu"]
 CPP_SOURCES = ["host.cpp", "tuning.cpp"]
 

@@ -286,6 +286,9 @@ struct iaat_plan_s {
     bool tw = false;               // warp-tile tensor-core kernel
     char *d_tw = nullptr;          // its warp tasks, per-warp ranges and error word
     TwParams twp{};
+    bool wd = false;               // warp-direct CUDA-core kernel
+    char *d_wd = nullptr;          // its warp tasks, per-warp ranges and error word
+    WdParams wdp{};
     int64_t ntasks = 0, ngroups = 0;
     int grid = 0;
     iaat_plan_info_t info{};
@@ -300,19 +303,21 @@ struct HostTask {
 };
 
 std::mutex g_prep_mutex;
-bool g_prepared[64][17];
+bool g_prepared[64][19];
 
 // kind: 0 = FP32 FFMA (stage programs), 1 = FP64 DFMA, 2..5 = tcgen05
 // precision (kind - 1), 6 = complex float, 7 = complex double, 8 = FP32 FFMA
 // warp-stream kernel, 9..12 = pack-stream tensor-core kernel, precision kind - 8,
-// 13..16 = warp-tile tensor-core kernel, precision kind - 12
+// 13..16 = warp-tile tensor-core kernel, precision kind - 12, 17 / 18 =
+// warp-direct kernel FP32 / FP64
 iaat_status_t prepare_device(int dev, int kind)
 {
     std::lock_guard<std::mutex> lk(g_prep_mutex);
     if (dev < 0 || dev >= 64)
         return fail(IAAT_ERR_CUDA, "device index %d out of range", dev);
     if (!g_prepared[dev][kind]) {
-        cudaError_t e = kind < 2    ? prepare_fma(kind)
+        cudaError_t e = kind > 16   ? prepare_wd(kind == 17 ? 4 : 8)
+                        : kind < 2  ? prepare_fma(kind)
                         : kind < 6  ? prepare_tc(kind - 1)
                         : kind == 8 ? prepare_ws()
                         : kind > 12 ? prepare_tw(kind - 12)
@@ -1592,6 +1597,186 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
 }
 
 
+// ------------------------------------------ warp-direct CUDA-core plans
+// (wd.cuh) Every instance is cut into row blocks of at most 32 rows and, per
+// row block of m rows, column blocks of at most wd_max_cols columns (at most
+// kWdChunkIters * g columns when K exceeds one pass); the warp's lanes form
+// g = floor(32 / m) column groups.  The blocks are dealt to the warps largest
+// estimated cost first, each to the least loaded warp.
+static double wd_task_cost(const WdTask &t, int esz)
+{
+    // issue slots of one warp, roughly: record and set-up; the row of op(A);
+    // the staging rounds (4 elements of op(B) and 4 C0 steps per lane each);
+    // per column step the k-loop (one FMA and a quarter or half of a 16-byte
+    // shared load per k) and the epilogue
+    const int K = t.K, kmax = wd_max_k(esz);
+    const int kr = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : kmax;
+    const int chunks = K > kmax ? (K + kmax - 1) / kmax : 1;
+    const double per_k = esz == 4 ? 1.25 : 1.5;
+    const int rb = (std::min(K, kmax) * t.n + 127) / 128, rc = (t.flags & kWdReadC) ? (t.iters + 3) / 4 : 0;
+    double c = 50.0 + (K > 0 ? chunks * (kr + 26.0 * std::max(rb, rc) + t.iters * (per_k * kr + 4.0)) : 26.0 * rc);
+    return c + t.iters * 8.0;
+}
+
+static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count, int esz,
+                                    const iaat_plan_options_t *opts, iaat_plan_t *out, const int64_t *index_map)
+{
+    std::vector<WdTask> tasks;
+    std::vector<double> cost;
+    tasks.reserve((size_t)count * 2);
+    cost.reserve((size_t)count * 2);
+    iaat_plan_info_t info{};
+    info.instances = count;
+    info.dtype = esz == 4 ? IAAT_F32 : IAAT_F64;
+    info.precision = IAAT_PREC_DEFAULT;
+    const int kmax = wd_max_k(esz), cmax = wd_max_cols(esz);
+    for (int64_t i = 0; i < count; ++i) {
+        const iaat_gemm_desc_t &g = descs[i];
+        const int64_t gi = index_map ? index_map[i] : i;
+        iaat_status_t st = check_instance(gi, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.transA, g.transB, g.A, g.B, g.C,
+                                          g.alpha, esz);
+        if (st != IAAT_OK)
+            return st;
+        const int M = g.M, N = g.N;
+        if (M == 0 || N == 0)
+            continue;
+        const int K = (g.alpha == 0.0) ? 0 : g.K;
+        if (K == 0 && g.beta == 1.0)
+            continue;   // C = 1*C: nothing to do
+        const bool readc = g.beta != 0.0;
+        info.active += 1;
+        info.flops += 2 * (int64_t)M * N * K;
+        info.algorithmic_bytes +=
+            ((int64_t)M * K + (int64_t)K * N + (int64_t)M * N + (readc ? (int64_t)M * N : 0)) * esz;
+        const double alpha = esz == 4 ? (double)(float)g.alpha : g.alpha;
+        const double beta = esz == 4 ? (double)(float)g.beta : g.beta;
+        const int nbm = (M + kWdMaxRows - 1) / kWdMaxRows;
+        for (int bi = 0; bi < nbm; ++bi) {
+            int r0, mh;
+            piece_range(M, nbm, bi, r0, mh);
+            const int gmax = 32 / mh;
+            const int ncap = std::min(cmax, K > kmax ? gmax * kWdChunkIters : cmax);
+            const int nbn = (N + ncap - 1) / ncap;
+            for (int bj = 0; bj < nbn; ++bj) {
+                int c0, nw;
+                piece_range(N, nbn, bj, c0, nw);
+                WdTask t{};
+                if (K > 0) {
+                    t.A = static_cast<const char *>(g.A) + (size_t)(g.transA ? (int64_t)r0 * g.lda : (int64_t)r0) * esz;
+                    t.B = static_cast<const char *>(g.B) + (size_t)(g.transB ? (int64_t)c0 : (int64_t)c0 * g.ldb) * esz;
+                }
+                t.C = static_cast<char *>(g.C) + (size_t)((int64_t)r0 + (int64_t)c0 * g.ldc) * esz;
+                t.lda = g.lda;
+                t.ldb = g.ldb;
+                t.ldc = g.ldc;
+                t.K = K;
+                t.m = (uint8_t)mh;
+                t.g = (uint8_t)std::min(gmax, nw);
+                t.iters = (uint8_t)((nw + t.g - 1) / t.g);
+                t.n = (uint16_t)nw;
+                t.magic = (uint16_t)((32768 + mh - 1) / mh);
+                t.flags = (uint8_t)((g.transA ? kWdTransA : 0) | (g.transB ? kWdTransB : 0) | (readc ? kWdReadC : 0));
+                if (esz == 4) {
+                    t.ab.f[0] = (float)alpha;
+                    t.ab.f[1] = (float)beta;
+                } else {
+                    t.ab.d[0] = alpha;
+                    t.ab.d[1] = beta;
+                }
+                tasks.push_back(t);
+                cost.push_back(wd_task_cost(t, esz));
+            }
+        }
+    }
+
+    iaat_plan_s *plan = new (std::nothrow) iaat_plan_s;
+    if (!plan)
+        return fail(IAAT_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e != cudaSuccess) {
+        delete plan;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    iaat_status_t ps = prepare_device(plan->device, esz == 4 ? 17 : 18);
+    if (ps != IAAT_OK) {
+        delete plan;
+        return ps;
+    }
+    plan->wd = true;
+    plan->esz = esz;
+    plan->dtype = esz == 4 ? IAAT_F32 : IAAT_F64;
+    plan->precision = IAAT_PREC_DEFAULT;
+    const int64_t nt = (int64_t)tasks.size();
+    const int sms = sm_count(plan->device);
+    const int grid = (int)std::min<int64_t>((nt + kWdWarps - 1) / kWdWarps, (int64_t)sms * kWdCtasPerSm);
+    const int nwarps = grid * kWdWarps;
+
+    std::vector<int32_t> wbeg((size_t)nwarps + 1, 0);
+    std::vector<WdTask> flat((size_t)nt);
+    if (nt > 0) {
+        std::vector<int32_t> order((size_t)nt);
+        for (int64_t k = 0; k < nt; ++k)
+            order[(size_t)k] = (int32_t)k;
+        std::stable_sort(order.begin(), order.end(), [&cost](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+        using Slot = std::pair<double, int32_t>;   // (load, rank of the warp)
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int r = 0; r < nwarps; ++r)
+            heap.push(Slot(0.0, r));
+        std::vector<int32_t> owner((size_t)nt);
+        std::vector<int32_t> per((size_t)nwarps, 0);
+        for (int32_t k : order) {
+            Slot sl = heap.top();
+            heap.pop();
+            const int r = sl.second;
+            const int w = (r % grid) * kWdWarps + r / grid;   // CTA r % grid, warp r / grid
+            owner[(size_t)k] = w;
+            ++per[(size_t)w];
+            sl.first += cost[(size_t)k];
+            heap.push(sl);
+        }
+        for (int w = 0; w < nwarps; ++w)
+            wbeg[(size_t)w + 1] = wbeg[(size_t)w] + per[(size_t)w];
+        std::vector<int32_t> fill(wbeg.begin(), wbeg.end() - 1);
+        for (int32_t k : order)
+            flat[(size_t)fill[(size_t)owner[(size_t)k]]++] = tasks[(size_t)k];
+        if (opts && opts->inject_fault == 1)
+            flat[0].m = 33;   // a record the kernel must refuse
+    }
+    const size_t tb = (size_t)std::max<int64_t>(nt, 1) * sizeof(WdTask);
+    const size_t wb = (((size_t)nwarps + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+    if ((e = cudaMalloc(&plan->d_wd, tb + wb + 256)) != cudaSuccess) {
+        plan->d_wd = nullptr;
+        iaat_plan_destroy(plan);
+        return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
+    }
+    if ((nt > 0 && (e = cudaMemcpy(plan->d_wd, flat.data(), (size_t)nt * sizeof(WdTask), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess) ||
+        (e = cudaMemcpy(plan->d_wd + tb, wbeg.data(), ((size_t)nwarps + 1) * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(plan->d_wd + tb + wb, 0, sizeof(int32_t))) != cudaSuccess) {
+        iaat_plan_destroy(plan);
+        return cuda_fail(e, "upload the warp tasks");
+    }
+    plan->wdp.tasks = reinterpret_cast<const WdTask *>(plan->d_wd);
+    plan->wdp.wbeg = reinterpret_cast<const int32_t *>(plan->d_wd + tb);
+    plan->wdp.err = reinterpret_cast<int32_t *>(plan->d_wd + tb + wb);
+    plan->wdp.nwarps = nwarps;
+    plan->d_err = plan->wdp.err;
+    plan->ntasks = nt;
+    plan->ngroups = nt > 0 ? nwarps : 0;
+    plan->grid = grid;
+    info.tasks = nt;
+    info.groups = plan->ngroups;
+    info.blocks = nt;
+    info.plan_bytes = (int64_t)(tb + wb + 256);
+    info.grid = grid;
+    info.kernels = nt > 0 ? 1 : 0;
+    info.kernel_family = 4;
+    plan->info = info;
+    *out = plan;
+    return IAAT_OK;
+}
+
 // Options that pin the stage programs' tiling or stages (a forced variant
 // or stage size, an injected fault) keep a plan on the stage programs alone.
 static bool opts_force_free(const iaat_plan_options_t *o)
@@ -1654,8 +1839,13 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     }
     (void)ctas_per_sm;
     int kernel = opts ? opts->kernel : 0;
-    if (kernel < 0 || kernel > 3)
+    if (kernel < 0 || kernel > 4)
         return fail(IAAT_ERR_INVALID_VALUE, "kernel %d out of range", kernel);
+    if (kernel == 4 && (tc || cplx))
+        return fail(IAAT_ERR_INVALID_VALUE,
+                    "kernel 4 (warp-direct CUDA-core kernel) takes FP32 or FP64 plans of the default precision");
+    if (kernel == 4)
+        return plan_create_wd(descs, count, esz, opts, out, index_map);
     if (kernel == 0 && dt == IAAT_F32)
         kernel = tuning().kernel[(int)precision];   // the autotuner's choice (0: stage programs)
     if (kernel == 3 && !tc)
@@ -1872,6 +2062,9 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
         return fail(IAAT_ERR_INVALID_VALUE, "route_k_below %d is negative", opts->route_k_below);
     if (opts && opts->route_mnk_below < 0)
         return fail(IAAT_ERR_INVALID_VALUE, "route_mnk_below %d is negative", opts->route_mnk_below);
+    if (opts && (opts->route_kernel < 0 || opts->route_kernel == 3 || opts->route_kernel > 4))
+        return fail(IAAT_ERR_INVALID_VALUE, "route_kernel %d is not a CUDA-core kernel family (0, 1, 2, 4)",
+                    opts->route_kernel);
     if (precision == IAAT_PREC_DEFAULT || !opts || (opts->route_k_below == 0 && opts->route_mnk_below == 0))
         return plan_create_impl(descs, count, dtype, precision, opts, nullptr, out);
 
@@ -1905,7 +2098,9 @@ extern "C" iaat_status_t iaat_plan_create(const iaat_gemm_desc_t *descs, int64_t
     if (st != IAAT_OK)
         return st;
     o.inject_fault = 0;
-    if (o.kernel == 3)
+    if (opts->route_kernel != 0)
+        o.kernel = opts->route_kernel;
+    else if (o.kernel == 3)
         o.kernel = 0;   // the CUDA-core part has no warp-tile kernel: its default plan
     st = plan_create_impl(dfma.data(), (int64_t)dfma.size(), IAAT_F32, IAAT_PREC_DEFAULT, &o, nullptr, &sub,
                           ifma.data());
@@ -1952,9 +2147,10 @@ extern "C" iaat_status_t iaat_gemm_grouped(iaat_plan_t plan, void *stream)
         return fail(IAAT_ERR_INVALID_VALUE, "plan is NULL");
     if (plan->ngroups == 0)
         return plan->sub ? iaat_gemm_grouped(plan->sub, stream) : IAAT_OK;
-    if (plan->ws || plan->tc2 || plan->tw) {
+    if (plan->ws || plan->tc2 || plan->tw || plan->wd) {
         const cudaStream_t s = static_cast<cudaStream_t>(stream);
         const cudaError_t e = plan->ws    ? launch_ws(plan->wsp, plan->grid, s)
+                              : plan->wd ? launch_wd(plan->esz, plan->wdp, plan->grid, s)
                               : plan->tw ? launch_tw((int)plan->precision, plan->twp, plan->grid, s)
                                          : launch_tc2((int)plan->precision, plan->t2p, plan->grid, s);
         if (e != cudaSuccess)
@@ -2044,8 +2240,10 @@ extern "C" iaat_status_t iaat_plan_destroy(iaat_plan_t plan)
         cudaFree(plan->d_prog);
     if (plan->d_poff)
         cudaFree(plan->d_poff);
-    if (plan->d_err && !plan->ws && !plan->tw)
+    if (plan->d_err && !plan->ws && !plan->tw && !plan->wd)
         cudaFree(plan->d_err);
+    if (plan->d_wd)
+        cudaFree(plan->d_wd);
     if (plan->d_ws)
         cudaFree(plan->d_ws);
     if (plan->d_tw)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "tw_types.cuh"
+#include "wd_types.cuh"
 #include "../../include/iaat.h"
 
 namespace iaat {
@@ -25,6 +26,9 @@ int tc2_ring_bytes(int precision);      // staging ring of one warp group (bytes
 cudaError_t prepare_tw(int precision);
 cudaError_t launch_tw(int precision, const TwParams &p, int grid, cudaStream_t stream);
 int tw_ring_bytes(int precision);       // staging ring of one warp (bytes)
+// warp-direct CUDA-core kernel (wd.cuh), esz 4 = FP32, 8 = FP64
+cudaError_t prepare_wd(int esz);
+cudaError_t launch_wd(int esz, const WdParams &p, int grid, cudaStream_t stream);
 // complex kernel (CGEMM / ZGEMM), dtype IAAT_C32 or IAAT_C64
 cudaError_t prepare_cplx(int dtype);
 cudaError_t launch_cplx(int dtype, const KParams &kp, int grid, cudaStream_t stream);

@@ -47,7 +47,7 @@ class PlanOptions(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("max_group_tasks", ctypes.c_int32),
                 ("force_variant", ctypes.c_int32), ("inject_fault", ctypes.c_int32),
                 ("route_k_below", ctypes.c_int32), ("kernel", ctypes.c_int32), ("route_mnk_below", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("route_kernel", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -179,12 +179,15 @@ class Plan:
 
 
 def iaat_plan_create(descs, dtype, precision=IAAT_PREC_DEFAULT, *, max_group_tasks=0, force_variant=0,
-                     inject_fault=0, route_k_below=0, kernel=0, route_mnk_below=0):
+                     inject_fault=0, route_k_below=0, kernel=0, route_mnk_below=0, route_kernel=0):
     """descs: numpy array of DESC_DTYPE (device pointers inside).  kernel
     (iaat_plan_options_t.kernel): 0 = default, 1 = stage-program kernels,
-    2 = stream kernels, 3 = warp-tile tensor-core kernel."""
+    2 = stream kernels, 3 = warp-tile tensor-core kernel, 4 = warp-direct
+    CUDA-core kernel; route_kernel: the family of a routed plan's CUDA-core
+    part."""
     descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
-    opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault, route_k_below, kernel, route_mnk_below)
+    opts = PlanOptions(0, max_group_tasks, force_variant, inject_fault, route_k_below, kernel, route_mnk_below,
+                       route_kernel)
     h = ctypes.c_void_p()
     _check(lib().iaat_plan_create(descs.ctypes.data if len(descs) else None, len(descs), dtype, precision,
                                   ctypes.byref(opts), ctypes.byref(h)))

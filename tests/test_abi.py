@@ -200,6 +200,23 @@ def test_routed_plan_validates_with_caller_indices(L):
     with pytest.raises(iaat.IaatError) as e:
         iaat.iaat_plan_create(d, iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_mnk_below=4096)
     assert e.value.status == 1 and "instance 3" in e.value.message
+    # the routed part's kernel family must be a CUDA-core one (0, 1, 2, 4)
+    for rk in (-1, 3, 5):
+        with pytest.raises(iaat.IaatError) as e:
+            iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, route_k_below=8, route_kernel=rk)
+        assert e.value.status == 1 and "route_kernel" in e.value.message
+
+
+def test_kernel_option_range(L):
+    """kernel 0..4; the warp-direct kernel (4) takes plans of the default
+    precision only; all refused before any device work."""
+    for k in (-1, 5):
+        with pytest.raises(iaat.IaatError) as e:
+            iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, kernel=k)
+        assert e.value.status == 1 and "kernel" in e.value.message
+    with pytest.raises(iaat.IaatError) as e:
+        iaat.iaat_plan_create(_desc(), iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, kernel=4)
+    assert e.value.status == 1 and "warp-direct" in e.value.message
 
 
 def test_pack_create_validates_before_the_device(L):
