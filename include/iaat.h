@@ -304,8 +304,11 @@ iaat_status_t iaat_plan_destroy(iaat_plan_t plan);
 
 /* Install-time tuning (Sec. III-A and Sec. IV: the kernels are tuned once
  * for the hardware they run on).  Times the register-tile variants on the
- * current GPU for (dtype, precision) and the stage size on an uneven batch,
- * and writes the per-variant cost scales and stage sizes as JSON to
+ * current GPU for (dtype, precision), the stage size on an uneven batch and,
+ * for FP32, the kernel family default plans run (FFMA: stage programs,
+ * stream or warp-direct; tensor cores: stage programs, stream or warp-tile;
+ * another family only when at least 3% faster than the stage programs),
+ * and writes the per-variant cost scales, stage sizes and families as JSON to
  * `cache_path` (NULL: the path in IAAT_TUNE_CACHE, else no file), together
  * with the GPU's name, SM count, driver and runtime versions.  Later
  * processes read the cache named by IAAT_TUNE_CACHE and ignore it when any

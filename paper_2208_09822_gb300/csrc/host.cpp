@@ -1598,24 +1598,25 @@ static iaat_status_t plan_create_tw(const iaat_gemm_desc_t *descs, int64_t count
 
 
 // ------------------------------------------ warp-direct CUDA-core plans
-// (wd.cuh) Every instance is cut into row blocks of at most 32 rows and, per
-// row block of m rows, column blocks of at most wd_max_cols columns (at most
-// kWdChunkIters * g columns when K exceeds one pass); the warp's lanes form
-// g = floor(32 / m) column groups.  The blocks are dealt to the warps largest
-// estimated cost first, each to the least loaded warp.
+// (wd.cuh) Every instance is cut into row blocks and, per row block of m
+// rows, column blocks; the warp's lanes form g = floor(32 / m) column groups.
+// Instances with K up to wd_k1 take blocks of at most 32 rows and
+// wd_max_cols columns, the others at most 16 rows and half the columns (their
+// longer op(A) rows and op(B) columns fit the same staging area).  The blocks
+// are dealt to the warps largest estimated cost first, each to the least
+// loaded warp.
 static double wd_task_cost(const WdTask &t, int esz)
 {
-    // issue slots of one warp, roughly: record and set-up; the row of op(A);
-    // the staging rounds (4 elements of op(B) and 4 C0 steps per lane each);
-    // per column step the k-loop (one FMA and a quarter or half of a 16-byte
-    // shared load per k) and the epilogue
-    const int K = t.K, kmax = wd_max_k(esz);
-    const int kr = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : kmax;
-    const int chunks = K > kmax ? (K + kmax - 1) / kmax : 1;
+    // issue slots of one warp, roughly: record and set-up; the staging
+    // copies (op(A) and op(B) per lane group of 32, C0 per column step); per
+    // column step the k-loop (one FMA and a quarter or half of a 16-byte
+    // shared load per k) and the epilogue; per extra K chunk a wait
+    const int K = t.K, k2 = wd_k2(esz);
     const double per_k = esz == 4 ? 1.25 : 1.5;
-    const int rb = (std::min(K, kmax) * t.n + 127) / 128, rc = (t.flags & kWdReadC) ? (t.iters + 3) / 4 : 0;
-    double c = 50.0 + (K > 0 ? chunks * (kr + 26.0 * std::max(rb, rc) + t.iters * (per_k * kr + 4.0)) : 26.0 * rc);
-    return c + t.iters * 8.0;
+    const int chunks = K > k2 ? (K + k2 - 1) / k2 : 1;
+    const double copies = std::ceil((double)K * (t.m + t.n) / 32.0) * 6.0 +
+                          ((t.flags & kWdReadC) ? t.iters * 5.0 : 0.0);
+    return 120.0 + copies + t.iters * (per_k * K + 12.0 + 6.0 * (chunks - 1)) + 60.0 * (chunks - 1);
 }
 
 static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count, int esz,
@@ -1629,7 +1630,7 @@ static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count
     info.instances = count;
     info.dtype = esz == 4 ? IAAT_F32 : IAAT_F64;
     info.precision = IAAT_PREC_DEFAULT;
-    const int kmax = wd_max_k(esz), cmax = wd_max_cols(esz);
+    const int k1 = wd_k1(esz), cmax = wd_max_cols(esz);
     for (int64_t i = 0; i < count; ++i) {
         const iaat_gemm_desc_t &g = descs[i];
         const int64_t gi = index_map ? index_map[i] : i;
@@ -1650,12 +1651,13 @@ static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count
             ((int64_t)M * K + (int64_t)K * N + (int64_t)M * N + (readc ? (int64_t)M * N : 0)) * esz;
         const double alpha = esz == 4 ? (double)(float)g.alpha : g.alpha;
         const double beta = esz == 4 ? (double)(float)g.beta : g.beta;
-        const int nbm = (M + kWdMaxRows - 1) / kWdMaxRows;
+        const bool wide = K > k1;
+        const int rcap = wide ? kWdRows2 : kWdMaxRows, ncap = wide ? cmax / 2 : cmax;
+        const int nbm = (M + rcap - 1) / rcap;
         for (int bi = 0; bi < nbm; ++bi) {
             int r0, mh;
             piece_range(M, nbm, bi, r0, mh);
             const int gmax = 32 / mh;
-            const int ncap = std::min(cmax, K > kmax ? gmax * kWdChunkIters : cmax);
             const int nbn = (N + ncap - 1) / ncap;
             for (int bj = 0; bj < nbn; ++bj) {
                 int c0, nw;
@@ -1844,10 +1846,10 @@ static iaat_status_t plan_create_impl(const iaat_gemm_desc_t *descs, int64_t cou
     if (kernel == 4 && (tc || cplx))
         return fail(IAAT_ERR_INVALID_VALUE,
                     "kernel 4 (warp-direct CUDA-core kernel) takes FP32 or FP64 plans of the default precision");
-    if (kernel == 4)
-        return plan_create_wd(descs, count, esz, opts, out, index_map);
     if (kernel == 0 && dt == IAAT_F32)
         kernel = tuning().kernel[(int)precision];   // the autotuner's choice (0: stage programs)
+    if (kernel == 4)
+        return plan_create_wd(descs, count, esz, opts, out, index_map);
     if (kernel == 3 && !tc)
         return fail(IAAT_ERR_INVALID_VALUE, "kernel 3 (warp-tile tensor-core kernel) needs a tensor-core precision");
     if (tc && kernel == 3)

@@ -89,7 +89,11 @@ void apply_text(const std::string &txt, Tuning &t)
     read_int(txt, "group_tasks_dfma", &t.group_tasks_f64, 1, kMaxGroupTasks);
     for (int i = 0; i < 5; ++i) {
         static const char *keys[5] = {"kernel_ffma", "kernel_3xbf16", "kernel_tf32", "kernel_fp16", "kernel_6xbf16"};
-        read_int(txt, keys[i], &t.kernel[i], 1, i == 0 ? 2 : 3);
+        int k = 0;
+        // FFMA: stage programs, stream or warp-direct; tensor cores: stage
+        // programs, stream or warp-tile
+        if (read_int(txt, keys[i], &k, 1, 4) && (i == 0 ? k != 3 : k != 4))
+            t.kernel[i] = k;
     }
     t.from_cache = a || b;
 }
@@ -396,7 +400,9 @@ extern "C" iaat_status_t iaat_autotune(iaat_dtype_t dtype, iaat_precision_t prec
         if (st == IAAT_OK && dtype == IAAT_F32) {
             best_kernel = 1;
             const double stage = best;
-            for (int k = 2; k <= (precision == IAAT_PREC_DEFAULT ? 2 : 3) && st == IAAT_OK; ++k) {
+            for (int k : {2, precision == IAAT_PREC_DEFAULT ? 4 : 3}) {
+                if (st != IAAT_OK)
+                    break;
                 iaat_plan_options_t o{};
                 o.kernel = k;
                 double ms = 0;

@@ -17,7 +17,7 @@ struct Tuning {
     int group_tasks_f64 = 0;             // same for FP64 (0: kMaxGroupTasks)
     // the kernel family a default FP32 plan (option kernel = 0) runs, by
     // iaat_precision_t: 1 stage programs, 2 stream, 3 warp-tile (tensor-core
-    // precisions only); 0: not tuned (stage programs)
+    // precisions only), 4 warp-direct (FFMA only); 0: not tuned (stage programs)
     int kernel[5] = {0, 0, 0, 0, 0};
     bool from_cache = false;
     Tuning()

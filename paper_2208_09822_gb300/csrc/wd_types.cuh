@@ -41,23 +41,35 @@ struct WdParams {
 
 constexpr int kWdWarps = 4;          // warps per CTA
 constexpr int kWdThreads = 32 * kWdWarps;
-constexpr int kWdCtasPerSm = 5;      // 20 warps per SM (96 registers a thread)
+constexpr int kWdCtasPerSm = 6;      // 24 warps per SM (80 registers a thread)
 constexpr int kWdMaxRows = 32;       // block height: one row per lane
-constexpr int kWdChunkIters = 8;     // column steps per lane when K runs in chunks
-// The largest K one pass holds in registers (larger K runs in chunks of it,
-// with at most kWdChunkIters column steps per lane) and the block width.
-IAAT_HD constexpr int wd_max_k(int esz) { return esz == 4 ? 32 : 16; }
+// Two block shapes.  Up to wd_k1 values of K: at most 32 rows and
+// wd_max_cols columns, row i of op(A) at sA[k*32 + i], op(B) column j at
+// sB[j*wd_pitch1].  Beyond: at most 16 rows and wd_max_cols / 2 columns,
+// K in passes of up to wd_k2 values (one pass, or chunks of wd_k2 with the
+// partial sums of the lane's at most 8 column steps kept between chunks),
+// row i at sA[k*16 + i], column j at sB[j*wd_pitch2].  Both fit the same
+// staging area.
+IAAT_HD constexpr int wd_k1(int esz) { return esz == 4 ? 16 : 8; }
+IAAT_HD constexpr int wd_k2(int esz) { return esz == 4 ? 32 : 16; }
 IAAT_HD constexpr int wd_max_cols(int esz) { return esz == 4 ? 32 : 16; }
-// Staged op(B) column pitch (elements) for a pass of kr values of K: at least
-// kr, a whole number of 16-byte groups, and an odd number of them (or one),
-// so that consecutive columns start in different 16-byte bank groups.
-IAAT_HD constexpr int wd_pitch(int esz, int kr) { return esz == 4 ? (kr == 4 ? 4 : kr + 4) : kr + 2; }
+constexpr int kWdRows2 = 16;         // block height beyond wd_k1
+constexpr int kWdChunkIters = 8;     // column steps per lane of a 16-row block (g >= 2)
+// Staged op(B) column pitches (elements): whole, odd numbers of 16-byte
+// groups, so that consecutive columns start in different 16-byte bank groups.
+IAAT_HD constexpr int wd_pitch1(int esz) { return esz == 4 ? 20 : 10; }
+IAAT_HD constexpr int wd_pitch2(int esz) { return esz == 4 ? 36 : 18; }
 // A warp's slice of shared memory: two task records (the next one lands
-// while the current block runs), the op(B) block, then 32 lanes' C0 values
-// per column step.
+// while the current block runs), the op(A) block, the op(B) block, then 32
+// lanes' C0 values per column step (rows 8..15 hold partial sums between K
+// chunks).
 constexpr int kWdRecBytes = 2 * (int)sizeof(WdTask);
-IAAT_HD constexpr int wd_b_elems(int esz) { return wd_max_cols(esz) * wd_pitch(esz, wd_max_k(esz)); }
-IAAT_HD constexpr int wd_stage_elems(int esz) { return wd_b_elems(esz) + wd_max_cols(esz) * 32; }
+IAAT_HD constexpr int wd_a_elems(int esz) { return wd_k1(esz) * kWdMaxRows; }   // == wd_k2 * kWdRows2
+IAAT_HD constexpr int wd_b_elems(int esz) { return wd_max_cols(esz) * wd_pitch1(esz); }
+IAAT_HD constexpr int wd_stage_elems(int esz) { return wd_a_elems(esz) + wd_b_elems(esz) + wd_max_cols(esz) * 32; }
 IAAT_HD constexpr int wd_warp_bytes(int esz) { return kWdRecBytes + wd_stage_elems(esz) * esz; }
+static_assert(wd_k2(4) * kWdRows2 <= wd_a_elems(4) && wd_k2(8) * kWdRows2 <= wd_a_elems(8), "op(A) fits");
+static_assert(wd_max_cols(4) / 2 * wd_pitch2(4) <= wd_b_elems(4) && wd_max_cols(8) / 2 * wd_pitch2(8) <= wd_b_elems(8),
+              "op(B) fits");
 
 }  // namespace iaat
