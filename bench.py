@@ -43,7 +43,7 @@ NOMINAL_HBM_GBS = 8000.0
 ROUTE = {"3xbf16-k8ffma": (8, 0, 0), "3xbf16-r8": (8, 8 ** 3, 0), "3xbf16-r12": (8, 12 ** 3, 0),
          "3xbf16-r16": (8, 16 ** 3, 0), "3xbf16-r24": (8, 24 ** 3, 0), "3xbf16-r32": (8, 32 ** 3, 0)}
 ROUTE.update({"3xbf16-k8d": (8, 0, 4)})
-ROUTE.update({f"3xbf16-r{n}d": (8, n ** 3, 4) for n in (8, 12, 16, 20, 24, 32)})
+ROUTE.update({f"3xbf16-r{n}d": (8, n ** 3, 4) for n in (8, 12, 16, 20, 24, 32, 40, 48, 64)})
 PRECISIONS = {"ffma": 0, "3xbf16": 1, "tf32": 2, "fp16": 3, "6xbf16": 4}
 PRECISIONS.update({n: 1 for n in ROUTE})
 # each path can also be forced onto one kernel family: name + "@stage"
@@ -449,9 +449,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="iaat", choices=["iaat", "reference"])
-    ap.add_argument("--precision", default="3xbf16-r20d", choices=sorted(PRECISIONS),
+    ap.add_argument("--precision", default="3xbf16-r32d", choices=sorted(PRECISIONS),
                     help="the headline path: by default the tensor-core FP32 split (3xBF16) on the instances "
-                         "with M*N*K >= 20^3 and K >= 8, the smaller ones on the FP32 CUDA cores (warp-direct "
+                         "with M*N*K >= 32^3 and K >= 8, the smaller ones on the FP32 CUDA cores (warp-direct "
                          "kernel)")
     ap.add_argument("--compare", default="ffma,ffma@direct,3xbf16,3xbf16-r16",
                     type=lambda v: [x for x in v.split(",") if x],

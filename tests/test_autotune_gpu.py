@@ -28,11 +28,23 @@ def cuda():
     return torch
 
 
+def autotune(path, *precisions):
+    """Tune in a child process: iaat_autotune also applies the result to the
+    process that calls it, which would change the default plans of every
+    later test in this one."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2208_09822_gb300 import iaat\n"
+            "for p in %r:\n"
+            "    iaat.iaat_autotune(iaat.IAAT_F32, p, %r)\n" % (ROOT, list(precisions), path))
+    env = dict(os.environ)
+    env.pop("IAAT_TUNE_CACHE", None)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
 def test_autotune_writes_cache_and_tuned_plans_stay_correct(tmp_path):
     path = str(tmp_path / "tune.json")
-    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, path)
-    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_3XBF16, path)
-    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_FP16, path)
+    autotune(path, iaat.IAAT_PREC_DEFAULT, iaat.IAAT_PREC_3XBF16, iaat.IAAT_PREC_FP16)
     cache = json.load(open(path))
     assert len(cache["variant_scale_f32"]) == 5
     assert all(v > 0 for v in cache["variant_scale_f32"])
@@ -70,7 +82,7 @@ def test_cache_applies_only_on_the_gpu_it_was_measured_on(tmp_path):
     A cache forcing 8 tasks per stage changes the plan's stage count; the
     same cache with another device name is ignored."""
     path = str(tmp_path / "tune.json")
-    iaat.iaat_autotune(iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, path)
+    autotune(path, iaat.IAAT_PREC_DEFAULT)
     cache = json.load(open(path))
     for key in ("device", "sm_count", "compute_capability", "driver_version", "runtime_version"):
         assert key in cache, key
