@@ -566,11 +566,29 @@ def main():
     dfma_bound = wl_dtype in (1, 3)
     dfma_peak = iaat.iaat_fma_peak(iaat.IAAT_F64) if dfma_bound else None
 
-    def time_path(name):
+    def route_split(d, name):
+        """The two parts of a routed path's descriptors, by the planner's rule
+        (K below route_k_below or M*N*K below route_mnk_below, alpha = 0
+        counting as K = 0): (tensor-core part, CUDA-core part)."""
+        rk, rm, _ = ROUTE[ROUTE_BASE(name)]
+        keff = np.where(d["alpha"] == 0.0, 0, d["K"]).astype(np.int64)
+        small = (keff < rk) | (d["M"].astype(np.int64) * d["N"] * keff < rm)
+        return d[~small], d[small]
+
+    def make_part(d, name, part):
+        """Plan of one part of a routed path, alone (what that part's launch
+        inside the routed plan runs)."""
+        big, small = route_split(d, name)
+        if part == 0:
+            return iaat.iaat_plan_create(big, iaat.IAAT_F32, PRECISIONS[name], kernel=KERNEL.get(name, 0))
+        return iaat.iaat_plan_create(small, iaat.IAAT_F32, iaat.IAAT_PREC_DEFAULT, kernel=ROUTE[ROUTE_BASE(name)][2])
+
+    def time_path(name, part=None):
         """First launch (kept for the error check), then a CUDA graph of one
         launch per pool copy (one launch when the pools exceed L2) replayed
-        between events on the launch stream, `steps` launches in all."""
-        plans = [make_plan(d[r0:r1], name) for d in descs_rot]
+        between events on the launch stream, `steps` launches in all.  With
+        `part` (0 tensor-core, 1 CUDA-core), one part of a routed path alone."""
+        plans = [make_plan(d[r0:r1], name) if part is None else make_part(d[r0:r1], name, part) for d in descs_rot]
         plan = plans[0]
         info = iaat.iaat_plan_info(plan)
         tC.copy_(C0)
@@ -625,6 +643,15 @@ def main():
     plan, info, ms, first_result = time_path(args.precision)
     clocks = sampler.stop()
     results[args.precision] = (info, ms, first_result)
+    # a routed path's two launches, each timed alone: the roofline below is
+    # the dominant one's (the path's own is kept beside it)
+    parts = []
+    if wl_dtype == 0 and ROUTE_BASE(args.precision) in ROUTE:
+        for part, kname in ((0, "tensor-core part"), (1, "CUDA-core part")):
+            plan_p, info_p, ms_p, _ = time_path(args.precision, part)
+            parts.append({"part": kname, "kernel_family": info_p.get("kernel_family"), "ms": ms_p,
+                          "instances": info_p["instances"], "algorithmic_bytes": info_p["algorithmic_bytes"]})
+            plan_p.destroy()
 
     flops = info["flops"]
     value = job_flops / (ms * 1e-3) / 1e9
@@ -759,6 +786,20 @@ def main():
                         "peak_kind": "measured DFMA rate (iaat_fma_peak, this GPU, at start-up)",
                         "algorithmic_bytes_per_launch": abytes,
                         "hbm_frac": achieved / peaks["hbm_gbs"]}
+        elif parts:
+            for pt in parts:
+                pt["achieved_gbs"] = pt["algorithmic_bytes"] / (pt["ms"] * 1e-3) / 1e9
+                pt["frac"] = pt["achieved_gbs"] / peaks["hbm_gbs"]
+            dom = max(parts, key=lambda pt: pt["ms"])
+            roofline = {"bound": "hbm", "achieved": dom["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": dom["frac"], "traffic": traffic,
+                        "peak_kind": f"{peak_kind} copy bandwidth",
+                        "kernel": f"{dom['part']} of the routed plan, timed alone",
+                        "algorithmic_bytes_per_launch": dom["algorithmic_bytes"],
+                        "path_achieved": achieved, "path_frac": achieved / peaks["hbm_gbs"],
+                        "path_algorithmic_bytes_per_step": abytes, "parts": parts,
+                        "roofline_gflops_at_8TBs": roof_gflops,
+                        "frac_of_8TBs_roofline": value / world / roof_gflops if roof_gflops else None}
         else:
             roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -781,8 +822,10 @@ def main():
                                                "no flush" % (pool_bytes / 1e6, rot, rot * pool_bytes / 1e6)),
                        "tasks": info["tasks"], "groups": info["groups"], "blocks": info["blocks"],
                        "grid": info["grid"], "tuning": tuned,
-                       "kernel_family": {1: "stage programs", 2: "stream", 3: "warp-tile"}.get(
-                           info.get("kernel_family"), "unknown")},
+                       "kernel_family": {1: "stage programs", 2: "stream", 3: "warp-tile", 4: "warp-direct"}.get(
+                           info.get("kernel_family"), "unknown") + (
+                           " + warp-direct (routed part)" if ROUTE.get(ROUTE_BASE(args.precision), (0, 0, 0))[2] == 4
+                           else "")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value if e2e_ok else None, "unit": "GFLOP/s", "ok": e2e_ok,

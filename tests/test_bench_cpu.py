@@ -35,13 +35,14 @@ def test_profiles_name_their_sources_and_command():
     sys.path.insert(0, ROOT)
     import bench
     for name in ("grouped_3xbf16_uneven200k.md", "grouped_ffma_uneven200k.md",
-                 "grouped_zgemm_uneven-c64100k.md"):
+                 "grouped_zgemm_uneven-c64100k.md", "grouped_3xbf16-r32d_uneven200k.md"):
         txt = open(os.path.join(ROOT, "profiles", name)).read()
         ncu = [ln for ln in txt.splitlines() if ln.startswith("ncu ")]
         assert "kernel_source_hash: " in txt and ncu, name
         assert all("--clock-control none" in ln and "--set full" in ln for ln in ncu), name
         args = {"grouped_3xbf16_uneven200k.md": ("3xbf16",), "grouped_ffma_uneven200k.md": ("ffma",),
-                "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000)}[name]
+                "grouped_zgemm_uneven-c64100k.md": ("zgemm", "uneven-c64", 100_000),
+                "grouped_3xbf16-r32d_uneven200k.md": ("3xbf16-r32d",)}[name]
         current = f"kernel_source_hash: {bench.kernel_source_hash(args[0])}" in txt
         traffic = bench.profile_traffic(*args)
         assert (traffic is not None and traffic > 0) == current, name
