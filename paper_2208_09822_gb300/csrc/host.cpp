@@ -1744,24 +1744,33 @@ static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count
         if (opts && opts->inject_fault == 1)
             flat[0].m = 33;   // a record the kernel must refuse
     }
+    // every warp's first task again, at a fixed place: the kernel fetches it
+    // without waiting for the warp's task range
+    std::vector<WdTask> first((size_t)std::max(nwarps, 1));
+    for (int w = 0; w < nwarps; ++w)
+        if (wbeg[(size_t)w] < wbeg[(size_t)w + 1])
+            first[(size_t)w] = flat[(size_t)wbeg[(size_t)w]];
     const size_t tb = (size_t)std::max<int64_t>(nt, 1) * sizeof(WdTask);
+    const size_t fb = first.size() * sizeof(WdTask);
     const size_t wb = (((size_t)nwarps + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
-    if ((e = cudaMalloc(&plan->d_wd, tb + wb + 256)) != cudaSuccess) {
+    if ((e = cudaMalloc(&plan->d_wd, tb + fb + wb + 256)) != cudaSuccess) {
         plan->d_wd = nullptr;
         iaat_plan_destroy(plan);
         return fail(IAAT_ERR_OOM, "cudaMalloc of the plan: %s", cudaGetErrorString(e));
     }
     if ((nt > 0 && (e = cudaMemcpy(plan->d_wd, flat.data(), (size_t)nt * sizeof(WdTask), cudaMemcpyHostToDevice)) !=
                        cudaSuccess) ||
-        (e = cudaMemcpy(plan->d_wd + tb, wbeg.data(), ((size_t)nwarps + 1) * sizeof(int32_t),
+        (e = cudaMemcpy(plan->d_wd + tb, first.data(), fb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(plan->d_wd + tb + fb, wbeg.data(), ((size_t)nwarps + 1) * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(plan->d_wd + tb + wb, 0, sizeof(int32_t))) != cudaSuccess) {
+        (e = cudaMemset(plan->d_wd + tb + fb + wb, 0, sizeof(int32_t))) != cudaSuccess) {
         iaat_plan_destroy(plan);
         return cuda_fail(e, "upload the warp tasks");
     }
     plan->wdp.tasks = reinterpret_cast<const WdTask *>(plan->d_wd);
-    plan->wdp.wbeg = reinterpret_cast<const int32_t *>(plan->d_wd + tb);
-    plan->wdp.err = reinterpret_cast<int32_t *>(plan->d_wd + tb + wb);
+    plan->wdp.first = reinterpret_cast<const WdTask *>(plan->d_wd + tb);
+    plan->wdp.wbeg = reinterpret_cast<const int32_t *>(plan->d_wd + tb + fb);
+    plan->wdp.err = reinterpret_cast<int32_t *>(plan->d_wd + tb + fb + wb);
     plan->wdp.nwarps = nwarps;
     plan->d_err = plan->wdp.err;
     plan->ntasks = nt;
@@ -1770,7 +1779,7 @@ static iaat_status_t plan_create_wd(const iaat_gemm_desc_t *descs, int64_t count
     info.tasks = nt;
     info.groups = plan->ngroups;
     info.blocks = nt;
-    info.plan_bytes = (int64_t)(tb + wb + 256);
+    info.plan_bytes = (int64_t)(tb + fb + wb + 256);
     info.grid = grid;
     info.kernels = nt > 0 ? 1 : 0;
     info.kernel_family = 4;

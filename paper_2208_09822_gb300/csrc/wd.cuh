@@ -302,11 +302,13 @@ __global__ void __launch_bounds__(kWdThreads, kWdCtasPerSm) wd_kernel(const WdPa
     const uint32_t uA = (uint32_t)__cvta_generic_to_shared(sA), uB = (uint32_t)__cvta_generic_to_shared(sB),
                    uC = (uint32_t)__cvta_generic_to_shared(sC);
     T *sP = sC + kWdChunkIters * 32;   // partial sums between K chunks (16-row blocks: steps < 8)
-    const int t0 = p.wbeg[w], t1 = p.wbeg[w + 1];
-    // records arrive by cp.async one block ahead: lanes 0..3 copy 16 bytes each
-    if (t0 < t1 && lane < 4)
-        wd_cp16(reinterpret_cast<char *>(sR) + 16 * lane, reinterpret_cast<const char *>(p.tasks + t0) + 16 * lane);
+    // records arrive by cp.async one block ahead, lanes 0..3 copying 16 bytes
+    // each; the first from the warp's own copy, in flight with the loads of
+    // its task range
+    if (lane < 4)
+        wd_cp16(reinterpret_cast<char *>(sR) + 16 * lane, reinterpret_cast<const char *>(p.first + w) + 16 * lane);
     wd_cp_commit();
+    const int t0 = p.wbeg[w], t1 = p.wbeg[w + 1];
     for (int t = t0; t < t1; ++t) {
         wd_cp_wait0();   // this block's record has landed
         __syncwarp();    // (and the previous block's reads of the staging area are done)

@@ -34,6 +34,8 @@ constexpr uint8_t kWdReadC = 4;
 struct WdParams {
     const WdTask *tasks;   // warp w's tasks: tasks[wbeg[w] .. wbeg[w+1])
     const int32_t *wbeg;
+    const WdTask *first;   // first[w]: a copy of warp w's first task (zeros if none), fetched
+                           // without waiting for wbeg
     int32_t *err;
     int32_t nwarps;        // warps of the grid that own tasks
     int32_t pad;
