@@ -56,6 +56,8 @@ for _n in list(PRECISIONS):
         PRECISIONS[_n + "@warp"] = PRECISIONS[_n]
     else:
         PRECISIONS[_n + "@direct"] = PRECISIONS[_n]
+# the FP64 batches' DFMA path, on the stage programs or the warp-direct kernel
+PRECISIONS.update({"dfma": 0, "dfma@direct": 0})
 KERNEL = {n: {"stage": 1, "stream": 2, "warp": 3, "direct": 4}.get(n.split("@")[1], 0) if "@" in n else 0
           for n in PRECISIONS}
 ROUTE_BASE = lambda n: n.split("@")[0]
@@ -509,9 +511,11 @@ def main():
     # this GPU before anything is timed; skipped when a tuning cache is given
     _, wl_desc, _, wl_dtype, wl_path, wl_tol = WORKLOADS[args.workload]
     if args.workload not in ("uneven", "uniform16"):
-        # other batches: their type's CUDA-core path alone
-        args.precision = wl_path
-        args.compare = []
+        # other batches: their type's CUDA-core path alone (the FP64 one on
+        # the stage programs or, asked for, the warp-direct kernel)
+        keep = lambda n: wl_dtype == 1 and ROUTE_BASE(n) == wl_path
+        args.precision = args.precision if keep(args.precision) else wl_path
+        args.compare = [n for n in args.compare if keep(n) and n != args.precision]
 
     tuned = "built-in cost model"
     if not args.no_autotune and not os.environ.get("IAAT_TUNE_CACHE") and wl_dtype in (0, 1):
@@ -559,7 +563,7 @@ def main():
             return iaat.iaat_plan_create(d, iaat.IAAT_F32, PRECISIONS[name], route_k_below=rk, route_mnk_below=rm,
                                          route_kernel=rf, kernel=KERNEL.get(name, 0))
         if wl_dtype == 1:
-            return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT)
+            return iaat.iaat_plan_create(d, iaat.IAAT_F64, iaat.IAAT_PREC_DEFAULT, kernel=KERNEL.get(name, 0))
         return iaat.iaat_plan_create_complex(d, wl_dtype)
 
     # the DFMA-bound batches are held against the measured DFMA rate
