@@ -79,3 +79,28 @@ def test_shard_split_bookkeeping(world):
                 assert lo <= first.min() and last.max() <= hi
             assert 0 <= lo <= hi <= pool.size
         assert cost[r["i0"]:r["i1"]].sum() <= cost.sum() / world + cost.max()
+
+
+def test_bench_paths_resolve():
+    """Every bench path names a precision the planner takes, a kernel family
+    its precision allows (warp-tile for the tensor cores only, warp-direct
+    for the CUDA cores only), a CUDA-core family for a routed part, and
+    translation units that exist (so its profile hash covers real sources)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_2208_09822_gb300", "csrc")
+    for name, prec in bench.PRECISIONS.items():
+        assert prec in (0, 1, 2, 3, 4), name
+        k = bench.KERNEL[name]
+        assert k in (0, 1, 2, 3, 4), name
+        assert not (k == 3 and prec == 0) and not (k == 4 and prec != 0), name
+        base = bench.ROUTE_BASE(name)
+        if base in bench.ROUTE:
+            rk, rm, rf = bench.ROUTE[base]
+            assert prec != 0 and rk >= 0 and rm >= 0 and rf in (0, 1, 2, 4), name
+        assert os.path.exists(os.path.join(csrc, bench.kernel_unit(name))), name
+        assert len(bench.kernel_source_hash(name)) == 16, name
+    # the headline is a routed tensor-core path with its small part on the
+    # warp-direct kernel; its hash covers both kernels' sources
+    assert bench.ROUTE["3xbf16-r32d"] == (8, 32 ** 3, 4)
+    assert bench.kernel_source_hash("3xbf16-r32d") != bench.kernel_source_hash("3xbf16")
